@@ -1,0 +1,446 @@
+"""Throughput benchmark: decoded information Gbit/s of the CI-schedule decoders
+on one GB300, next to flooding BP at equal FER and the CPU oracle.
+
+Workload (default): the WiFi-like rate-1/2 QC code (12x24 protograph, Z=96,
+n=2304, E=7776, k=1152), BPSK/AWGN at Eb/N0 = 2.0 dB, FP32 sum-product,
+ME-LMD-CIRBP (Algorithm 6) with N_P = 64, N_G = 16, budget 5 iteration
+equivalents (5E committed messages), syndrome checked after every step.
+One step = channel kernel (Philox AWGN LLRs) + decode of one batch of 65,536
+frames; LLR inputs (604 MB) exceed L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT_NOMINAL = 152
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 B
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--schedule", default="me-lmd-cirbp")
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--ebn0", type=float, default=2.0)
+    ap.add_argument("--budget-iters", type=float, default=5.0)
+    ap.add_argument("--n-p", type=int, default=64)
+    ap.add_argument("--n-g", type=int, default=16)
+    ap.add_argument("--arith", default="fp32")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2102_11089_gb300 import workloads as wl
+    d = wl.wifi_like(2, 96)
+    return d, 96
+
+
+def config_dict(args, code):
+    return {"workload": "wifi-like-qc-n2304-rate1/2", "code": "12x24 protograph, Z=96",
+            "n": code.N, "k": code.K, "edges": code.E, "ebn0_db": args.ebn0,
+            "schedule": args.schedule, "n_p": args.n_p, "n_g": args.n_g,
+            "budget_updates": int(args.budget_iters * code.E), "batch_frames": args.batch,
+            "arith": args.arith, "l2": "inputs larger than L2 (LLR batch %.0f MB)" %
+            (args.batch * code.N * 4 / 1e6), "parallelism": f"frames sharded, dp{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling
+
+
+class Clocks:
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [s for s in self.samples if len(s) >= 9 and s[0] == str(gpu_index)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work model (per committed update, FP32 state in shared memory)
+
+
+def bytes_per_update(code, arith):
+    """Shared-memory bytes of one committed C2V update, from the per-update
+    work of Table I with the code's average degrees (dv, dc):
+      CN selection   2 msg reads on each of the dv edges into n*
+      commit         read L~^C, write L^C, read/write L_n*, write D_n*
+      V2C inputs     (dv-1) refreshed checks x dc edges: read L_j and L^C
+      C2V outputs    (dv-1)(dc-1) writes of L~^C
+      CI update      (dv-1)(dc-1) x (dv reads of L~^C + L_j + lambda_j, write L~_j, D_j)
+    """
+    m = 4 if arith == "fp32" else 1
+    l = 4 if arith == "fp32" else 2
+    dv = code.E / code.N
+    dc = code.E / code.M
+    sel = 2 * m * dv
+    commit = 2 * m + 3 * l
+    v2c = (dv - 1) * dc * (l + m)
+    c2v = (dv - 1) * (dc - 1) * m
+    ci = (dv - 1) * (dc - 1) * (dv * m + 2 * l + 2 * l)
+    return sel + commit + v2c + c2v + ci
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def dist_max(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+
+
+def cpu_baseline(args, design, Z, seconds):
+    import oracle
+    from paper_2102_11089_gb300 import workloads as wl
+    base = design.shifts(Z)
+    chk, var = oracle.qc_lift(base, Z)
+    M, N = base.shape[0] * Z, base.shape[1] * Z
+    K = design.info_cols * Z
+    E = len(chk)
+    cores = os.cpu_count() or 1
+    sch = args.schedule
+    budget = int(args.budget_iters * E)
+    frames = 0
+    t0 = time.perf_counter()
+    el = 0.0
+    batch = cores
+    seed = 90000
+    while el < seconds and frames < 4096:
+        lam = oracle.awgn_llr(N, K / N, np.full(batch, args.ebn0), seed=seed, frame_offset=frames)
+        if args.arith == "int6":
+            q = oracle.quantize(lam.astype(np.float32), 0.5)
+            oracle.decode(chk, var, M, N, qllr=q, schedule=sch, max_updates=budget, n_p=args.n_p,
+                          n_g=args.n_g, threads=cores)
+        else:
+            oracle.decode(chk, var, M, N, llr=lam, schedule=sch, max_updates=budget, n_p=args.n_p,
+                          n_g=args.n_g, threads=cores)
+        frames += batch
+        el = time.perf_counter() - t0
+    return {"value": frames * K / el / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "sample": f"{frames} frames of the same workload ({sch}, FP64 oracle, one frame per "
+                      f"thread), {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    from paper_2102_11089_gb300 import workloads as wl
+    import oracle
+    oracle.build()
+    design, Z = workload(args)
+
+    class _C:
+        pass
+    code = _C()
+    sz = design.sizes(Z)
+    code.N, code.K, code.E, code.M = sz["N"], sz["K"], sz["E"], sz["M"]
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(args, design, Z, per_step / 4)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args, design, Z, per_step))
+    el = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    line = {"metric": "decoded info Gbit/s on 1 GB300 at fixed FER & update budget; vs flooding BP",
+            "value": v, "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, code), "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "Gbit/s", "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def fer_of(out):
+    hard = out["hard"]
+    return float((hard.sum(1) > 0).float().mean().item())
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2102_11089_gb300 as L
+
+    design, Z = workload(args)
+    code = L.Code.from_protograph(design.shifts(Z), Z, design.info_cols * Z, design.punct_cols)
+    B, N, K, E = args.batch, code.N, code.K, code.E
+    budget = int(args.budget_iters * E)
+    params = L.make_params(args.schedule, args.arith, gamma=0.1, n_p=args.n_p, n_g=args.n_g,
+                           max_updates=budget, check_interval=1, seed=1234)
+    stream = torch.cuda.current_stream()
+    eb = torch.full((B,), args.ebn0, dtype=torch.float32, device=device)
+    llr = torch.empty((B, N), dtype=torch.float32, device=device)
+    qllr = torch.empty((B, N), dtype=torch.int8, device=device) if args.arith == "int6" else None
+    out = dict(hard=torch.empty((B, N), dtype=torch.uint8, device=device),
+               updates=torch.empty(B, dtype=torch.int64, device=device),
+               converged=torch.empty(B, dtype=torch.uint8, device=device))
+    frame_base = rank * (10 ** 9)
+    dec_ev = []
+
+    def step(i, record=False):
+        off = frame_base + i * B
+        L.awgn_llr(code, eb, seed=2021, frame_offset=off, out=llr, qout=qllr,
+                   quantize=qllr is not None, stream=stream)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        L.decode(code, qllr if qllr is not None else llr, params, out=out, stream=stream)
+        if record:
+            e1.record(stream)
+            dec_ev.append((e0, e1))
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    L.sync(stream)
+    clocks = Clocks()
+    clocks.start()
+    upd_total = 0
+    barrier(world, device)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    upd_list = []
+    for i in range(args.steps):
+        step(args.warmup + i, record=True)
+        upd_list.append(out["updates"].sum())  # device-side reduction, read after timing
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, device)
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop(local)
+    upd_total = int(sum(int(u.item()) for u in upd_list))
+    fer = fer_of(out)
+    conv = float((out["converged"] & 1).float().mean().item())
+    mean_upd = float(out["updates"].float().mean().item())
+    ms_max = dist_max(ms, world, device)
+    value = world * B * args.steps * K / (ms_max * 1e-3) / 1e9
+    dec_ms = [a.elapsed_time(b) for a, b in dec_ev]
+    dec_avg = float(np.mean(dec_ms))
+
+    # ---- roofline of the decode kernel: algorithmic shared-memory bytes / time
+    peaks, peaks_kind = measured_peaks()
+    bpu = bytes_per_update(code, args.arith)
+    alg_bytes = bpu * upd_total / args.steps
+    achieved = alg_bytes / (dec_avg * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(device)
+    sm_count = props.multi_processor_count
+    clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    smem_peak = sm_count * SMEM_BYTES_PER_CLK_PER_SM * clk_mhz * 1e6 / 1e9
+    roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": achieved / smem_peak, "traffic": None,
+                "peak_source": f"derived: {sm_count} SMs x 128 B/clk x median SM clock "
+                               f"{clk_mhz:.0f} MHz (shared memory is not in MEASURED_PEAKS)",
+                "kernel": f"me_decode_kernel ({args.schedule}, {args.arith})",
+                "bytes_per_update": bpu, "updates_per_launch": upd_total / args.steps,
+                "launch_ms": dec_avg, "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks": peaks_kind}
+
+    # ---- end to end through host buffers: H2D Eb/N0 values, D2H decisions + counters
+    eb_host = torch.full((B,), args.ebn0, dtype=torch.float32).pin_memory()
+    hard_host = torch.empty((B, N), dtype=torch.uint8).pin_memory()
+    upd_host = torch.empty(B, dtype=torch.int64).pin_memory()
+    conv_host = torch.empty(B, dtype=torch.uint8).pin_memory()
+    e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier(world, device)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for i in range(e_steps):
+        eb.copy_(eb_host, non_blocking=True)
+        step(args.warmup + args.steps + i)
+        hard_host.copy_(out["hard"], non_blocking=True)
+        upd_host.copy_(out["updates"], non_blocking=True)
+        conv_host.copy_(out["converged"], non_blocking=True)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = dist_max(s0.elapsed_time(s1), world, device)
+    e2e = {"value": world * B * e_steps * K / (e2e_ms * 1e-3) / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": B * 4, "d2h_bytes_per_step": B * N + B * 8 + B,
+           "api": "ldpc_awgn_llr + ldpc_decode on one stream, pinned host buffers"}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(args, L, code, device, stream, fer, budget, value)
+
+    # launches: channel + decode per step
+    launches = 2 * args.steps
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline(args, design, Z, args.cpu_seconds)
+    if rank == 0:
+        line = {"metric": "decoded info Gbit/s on 1 GB300 at fixed FER & update budget; vs flooding BP",
+                "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.arith == "fp32" else "int8",
+                "data": "synthetic (seeded Philox AWGN, all-zero codeword, seeded stand-in code)",
+                "config": config_dict(args, code), "fer": fer, "frames_converged": conv,
+                "mean_updates_per_frame": mean_upd, "decode_ms_per_launch": dec_avg,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, **extras}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def time_decode(L, code, x, params, reps=3):
+    import torch
+    out = L.decode(code, x, params)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = L.decode(code, x, params, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), out
+
+
+def run_extras(args, L, code, device, stream, fer_ci, budget, value):
+    """Flooding at equal FER and the single-edge LMD-CIRBP on a sub-batch."""
+    import torch
+    B2 = min(args.batch, 8192)
+    eb = torch.full((B2,), args.ebn0, dtype=torch.float32, device=device)
+    llr, q = L.awgn_llr(code, eb, seed=2021, frame_offset=0, quantize=args.arith == "int6")
+    x = q if args.arith == "int6" else llr
+    res = {}
+    p_ci = L.make_params(args.schedule, args.arith, gamma=0.1, n_p=args.n_p, n_g=args.n_g,
+                         max_updates=budget, check_interval=1, seed=1234)
+    ms_ci, o_ci = time_decode(L, code, x, p_ci, reps=1)
+    f_ci = fer_of(o_ci)
+    flood = None
+    for it in list(range(1, 21)) + [25, 30, 40, 50]:
+        p = L.make_params("flooding", args.arith, max_updates=it * code.E, check_interval=code.E)
+        ms, o = time_decode(L, code, x, p, reps=1)
+        f = fer_of(o)
+        if f <= f_ci:
+            ms, o = time_decode(L, code, x, p, reps=3)
+            flood = {"iterations": it, "fer": f, "ms": ms,
+                     "gbit_s": B2 * code.K / (ms * 1e-3) / 1e9}
+            break
+    res["flooding_equal_fer"] = flood if flood else {"reached": False, "fer_ci": f_ci}
+    res["ci_subbatch"] = {"frames": B2, "fer": f_ci, "ms": ms_ci,
+                          "gbit_s": B2 * code.K / (ms_ci * 1e-3) / 1e9}
+    B3 = min(B2, 2048)
+    p_se = L.make_params("lmd-cirbp", args.arith, gamma=0.1, max_updates=budget, check_interval=1)
+    ms_se, o_se = time_decode(L, code, x[:B3].contiguous(), p_se, reps=1)
+    res["single_edge_lmd_cirbp"] = {"frames": B3, "fer": fer_of(o_se), "ms": ms_se,
+                                    "gbit_s": B3 * code.K / (ms_se * 1e-3) / 1e9}
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

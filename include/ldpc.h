@@ -1,0 +1,187 @@
+/*
+ * ldpc.h -- C ABI of the GB300 (sm_103a) dynamic-schedule LDPC decoder.
+ *
+ * The library decodes binary LDPC codes by belief propagation (BP) under the
+ * variable-node-centric dynamic schedules of T. C.-Y. Chang et al.,
+ * "Belief-Propagation Decoding of LDPC Codes with Variable Node-Centric
+ * Dynamic Schedules" (arXiv 2102.11089):
+ *   - CIRBP (Algorithm 1), LMD-CIRBP (Algorithm 3),
+ *   - the multi-edge ME-CIRBP (Algorithm 5) and ME-LMD-CIRBP (Algorithm 6)
+ *     with the VN selection of Algorithm 4,
+ * next to flooding BP (Sec. 1) and the original residual BP (Sec. 2.A).
+ *
+ * Conventions
+ *   - Every function returns ldpc_status_t: 0 on success, a negative code on
+ *     failure.  No function throws or aborts across this boundary.  A failed
+ *     call leaves its outputs unspecified and records a one-line reason
+ *     readable with ldpc_last_error_detail() (thread-local).
+ *   - Host pointers ("host") are read during the call only; the caller keeps
+ *     ownership.  Device pointers ("device") are CUDA global-memory addresses
+ *     on the current device, owned by the caller, and must stay valid until the
+ *     work enqueued on `cuda_stream` has finished.
+ *   - `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Decode
+ *     and channel calls are asynchronous on that stream; argument validation is
+ *     synchronous.  Errors found by kernels (non-finite or out-of-range inputs)
+ *     set per-frame flags and a per-device status word read by ldpc_sync().
+ *   - Edge ids are positions in the canonical order: edges sorted by check
+ *     index, then by variable index (the CSR order of H).
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ldpc_status_t;
+
+#define LDPC_OK 0
+#define LDPC_ERR_INVALID_ARG (-1)    /* NULL where not allowed, bad size or enum */
+#define LDPC_ERR_DUPLICATE_EDGE (-2) /* an (m, n) pair listed twice             */
+#define LDPC_ERR_INDEX_RANGE (-3)    /* check or variable index out of range    */
+#define LDPC_ERR_EMPTY_NODE (-4)     /* a check or variable node without edges  */
+#define LDPC_ERR_UNSUPPORTED (-5)    /* code or parameters beyond every form    */
+#define LDPC_ERR_CUDA (-6)           /* a CUDA runtime call failed              */
+#define LDPC_ERR_NOMEM (-7)          /* host or device allocation failed        */
+#define LDPC_ERR_TIMEOUT (-8)        /* a bounded device wait gave up           */
+#define LDPC_ERR_NONFINITE_LLR (-9)  /* a decode saw a NaN/Inf or out-of-range LLR */
+
+/* schedules (ldpc_decode_params_t.schedule) */
+#define LDPC_FLOODING 0     /* flooding BP: all V2C, then all C2V (Sec. 1)          */
+#define LDPC_RBP 1          /* residual BP, steps 1-4 of Sec. 2.A, eq. (5)          */
+#define LDPC_CIRBP 2        /* Algorithm 1 (CI metric eq. (8), threshold gamma)     */
+#define LDPC_LMD_CIRBP 3    /* Algorithm 3 (latest-message-driven CIRBP)            */
+#define LDPC_ME_CIRBP 4     /* Algorithm 5 (N_P edges per step, Algorithm 4)        */
+#define LDPC_ME_LMD_CIRBP 5 /* Algorithm 6                                          */
+
+/* arithmetic (ldpc_decode_params_t.arith) */
+#define LDPC_FP32_SUMPRODUCT 0 /* eq. (2) in FP32; input LLRs are float          */
+#define LDPC_INT6_MINSUM 1     /* min-sum (Sec. 5) on 6-bit integer LLRs (int8)  */
+
+/* execution forms (ldpc_decode_params_t.form) */
+#define LDPC_FORM_AUTO 0   /* pick by code size                                   */
+#define LDPC_FORM_SMEM 1   /* frame state in shared memory (warp or CTA / frame)  */
+#define LDPC_FORM_GLOBAL 2 /* frame state in device global memory (large codes)   */
+
+/* per-frame flag bits written to `converged` */
+#define LDPC_FRAME_CONVERGED 1u /* final hard decision satisfies every check      */
+#define LDPC_FRAME_BAD_INPUT 2u /* non-finite / out-of-range LLR: frame not decoded */
+
+typedef struct ldpc_code ldpc_code_t;
+
+typedef struct {
+    int32_t n_checks;      /* M                                                  */
+    int32_t n_vars;        /* N (all variable nodes, punctured ones included)    */
+    int64_t n_edges;       /* E = number of h_mn = 1                             */
+    int32_t k_info;        /* information bits per frame used for throughput     */
+    int32_t n_punctured;   /* variable nodes flagged as not transmitted          */
+    int32_t max_vn_degree; /* max |M(n)|                                         */
+    int32_t max_cn_degree; /* max |N(m)|                                         */
+    int32_t max_two_hop;   /* max over n of sum_{m in M(n)} |N(m)|               */
+    int32_t qc_lifting;    /* Z for codes built by ldpc_code_build_qc, else 0    */
+} ldpc_code_info_t;
+
+typedef struct {
+    int32_t schedule;       /* LDPC_FLOODING .. LDPC_ME_LMD_CIRBP                 */
+    int32_t arith;          /* LDPC_FP32_SUMPRODUCT or LDPC_INT6_MINSUM           */
+    double gamma;           /* CIRBP threshold on D (Alg. 1 line 5), in [0, 1)    */
+    int32_t n_p;            /* multi-edge: VNs updated per step (N_P, Sec. 6)     */
+    int32_t n_g;            /* multi-edge: CI groups of Algorithm 4 (N_G)         */
+    int64_t max_updates;    /* budget in committed C2V messages (E = 1 iteration,
+                               Sec. 2.A); flooding uses whole iterations only     */
+    int64_t check_interval; /* syndrome checked at 0 updates and whenever the
+                               count crosses a multiple of this (0 = never)       */
+    float llr_clip;         /* FP32: V2C inputs and C2V outputs clipped to +-this */
+    float q_step;           /* INT6: LLR value of one quantisation step (Delta)   */
+    uint64_t seed;          /* Algorithm 4 random fill (Philox4x32-10 key)         */
+    uint64_t frame_offset;  /* global index of frame 0 of this batch (Philox ctr)  */
+    int32_t form;           /* LDPC_FORM_*                                        */
+    int32_t reserved;       /* must be 0                                          */
+} ldpc_decode_params_t;
+
+/* Name of a status code (static string). */
+const char *ldpc_status_string(ldpc_status_t status);
+
+/* One-line description of the last failure on this thread ("" if none). */
+const char *ldpc_last_error_detail(void);
+
+/* Fill `p` with the defaults: LMD-CIRBP, FP32, gamma 0.1 (Sec. 5.A), N_P 16,
+ * N_G 16, budget 0 (caller must set), check_interval 1, llr_clip 25,
+ * q_step 0.5, seed 0, frame_offset 0, form AUTO. */
+ldpc_status_t ldpc_default_params(ldpc_decode_params_t *p);
+
+/* Build a code from the edge list of H (Sec. 2.A: h_mn = 1 <=> edge (m, n)).
+ * check_idx, var_idx : host int32[n_edges], 0 <= check < n_checks, 0 <= var < n_vars
+ * punctured          : host uint8[n_vars] or NULL; nonzero = not transmitted
+ *                      (the 5G NR codes of Sec. 5 puncture their first 2Z VNs)
+ * k_info             : information bits per frame (> 0)
+ * out                : receives the handle; the library copies every array.
+ * Errors: INVALID_ARG (NULL arrays, sizes <= 0), INDEX_RANGE, DUPLICATE_EDGE,
+ * EMPTY_NODE (every check and variable needs an edge), NOMEM.
+ * Host only: no device memory is touched until the first decode on a device. */
+ldpc_status_t ldpc_code_create(const int32_t *check_idx, const int32_t *var_idx, int64_t n_edges,
+                               int32_t n_checks, int32_t n_vars, const uint8_t *punctured,
+                               int32_t k_info, ldpc_code_t **out);
+
+/* Build a quasi-cyclic code by circulant lifting of a protograph.
+ * base       : host int32[rows * cols], row-major; -1 = zero block, s >= 0 =
+ *              Z x Z circulant whose row z has its one in column (z + s) mod Z,
+ *              i.e. edges (r Z + z, c Z + (z + s) mod Z) for z = 0..Z-1
+ * punct_cols : host uint8[cols] or NULL; nonzero = every VN of that column punctured
+ * k_info     : information bits per frame (> 0)
+ * Errors as ldpc_code_create, plus INVALID_ARG for s >= Z or Z <= 0. */
+ldpc_status_t ldpc_code_build_qc(const int32_t *base, int32_t rows, int32_t cols, int32_t Z,
+                                 const uint8_t *punct_cols, int32_t k_info, ldpc_code_t **out);
+
+/* Release a code and its device copies.  NULL is accepted. */
+ldpc_status_t ldpc_code_destroy(ldpc_code_t *code);
+
+/* Sizes and degree statistics of a code. */
+ldpc_status_t ldpc_code_info(const ldpc_code_t *code, ldpc_code_info_t *out);
+
+/* The canonical edge list: check_out, var_out are host int32[n_edges]
+ * receiving edge e = (check_out[e], var_out[e]); used to decode traces. */
+ldpc_status_t ldpc_code_edges(const ldpc_code_t *code, int32_t *check_out, int32_t *var_out);
+
+/* BPSK/AWGN channel (Sec. 2.A, Sec. 5) for the all-zero codeword: x = +1,
+ * y = 1 + sigma w, N0/2 = sigma^2 = 1 / (2 R 10^(EbN0/10)) with R = k_info / N_tx
+ * (N_tx = unpunctured VNs), LLR lambda = 2 y / sigma^2, punctured VNs 0.
+ * w: Box-Muller on Philox4x32-10 (key = seed, counter = (n / 4, 0, frame)),
+ * frame = frame_offset + b; VNs 4k..4k+3 share one Philox block.
+ * ebn0_db : device float[batch]       llr  : device float[batch][n_vars]
+ * qllr    : device int8[batch][n_vars] or NULL: clamp(rint(lambda/q_step), -31, 31)
+ * Errors: INVALID_ARG, CUDA. */
+ldpc_status_t ldpc_awgn_llr(const ldpc_code_t *code, const float *ebn0_db, int64_t batch,
+                            uint64_t seed, uint64_t frame_offset, float *llr, int8_t *qllr,
+                            float q_step, void *cuda_stream);
+
+/* Decode `batch` independent frames.
+ * llr       : device [batch][n_vars]; float for FP32, int8 in [-31, 31] for INT6
+ * params    : host; schedule, arithmetic and budget (see ldpc_decode_params_t)
+ * hard      : device uint8[batch][n_vars] or NULL: bsgn(L_n), 0 if L_n >= 0 (Sec. 2.A)
+ * updates   : device int64[batch] or NULL: committed C2V messages at the stop
+ * converged : device uint8[batch] or NULL: LDPC_FRAME_* flags
+ * trace     : device int32[batch][max_updates] or NULL: committed edge id per
+ *             update (multi-edge: each step's ids in ascending VN order);
+ *             entries past `updates` are left untouched; flooding writes none
+ * llr_out   : device float[batch][n_vars] or NULL: final total LLR L_n, eq. (3)
+ *             (INT6: the integer value)
+ * Stops at a zero syndrome (checked per check_interval) or at the budget.
+ * Errors: INVALID_ARG, UNSUPPORTED (no execution form fits), CUDA, NOMEM. */
+ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batch,
+                          const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
+                          uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);
+
+/* Wait for `cuda_stream` and return the device status accumulated by decode
+ * calls on the current device since the previous ldpc_sync (the status word
+ * is then cleared): LDPC_OK, LDPC_ERR_NONFINITE_LLR, LDPC_ERR_TIMEOUT or
+ * LDPC_ERR_CUDA for a failed stream. */
+ldpc_status_t ldpc_sync(void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_H */

@@ -1,0 +1,451 @@
+// api.cpp -- the C ABI (include/ldpc.h): code handles, validation, dispatch.
+#include "ldpc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_detail;
+
+ldpc_status_t fail(ldpc_status_t st, const std::string& why) {
+  g_detail = why;
+  return st;
+}
+
+ldpc_status_t cuda_fail(cudaError_t e, const char* where) {
+  return fail(LDPC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+struct DevCopy {
+  int32_t* buf = nullptr;  // cn_ptr | e_vn | e_cn | vn_ptr | vn_e
+  uint8_t* punct = nullptr;
+  ldpc::DevCode g{};
+};
+
+std::mutex g_status_mu;
+std::map<int, uint32_t*> g_status;  // per-device status word
+
+ldpc_status_t device_status_word(int dev, uint32_t** out) {
+  std::lock_guard<std::mutex> lk(g_status_mu);
+  auto it = g_status.find(dev);
+  if (it != g_status.end()) {
+    *out = it->second;
+    return LDPC_OK;
+  }
+  uint32_t* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+  e = cudaMemset(p, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+  g_status[dev] = p;
+  *out = p;
+  return LDPC_OK;
+}
+
+}  // namespace
+
+struct ldpc_code {
+  int32_t M = 0, N = 0, E = 0, K = 0, Z = 0;
+  int32_t dv_max = 0, dc_max = 0, maxr = 0, n_punct = 0;
+  std::vector<int32_t> cn_ptr, e_vn, e_cn, vn_ptr, vn_e;
+  std::vector<uint8_t> punct;
+  std::mutex mu;
+  std::map<int, DevCopy> dev;
+};
+
+namespace {
+
+ldpc_status_t build_code(const int32_t* chk, const int32_t* var, int64_t n_edges, int32_t M, int32_t N,
+                         const uint8_t* punct, int32_t k_info, int32_t Z, ldpc_code_t** out) {
+  if (!out) return fail(LDPC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!chk || !var) return fail(LDPC_ERR_INVALID_ARG, "edge arrays are NULL");
+  if (n_edges <= 0 || M <= 0 || N <= 0) return fail(LDPC_ERR_INVALID_ARG, "sizes must be positive");
+  if (n_edges > (int64_t)M * (int64_t)N) return fail(LDPC_ERR_DUPLICATE_EDGE, "more edges than cells of H");
+  if (n_edges > 0x7fffffff) return fail(LDPC_ERR_UNSUPPORTED, "more than 2^31-1 edges");
+  if (k_info <= 0) return fail(LDPC_ERR_INVALID_ARG, "k_info must be positive");
+  std::vector<int64_t> key;
+  try {
+    key.resize((size_t)n_edges);
+  } catch (const std::bad_alloc&) {
+    return fail(LDPC_ERR_NOMEM, "host allocation");
+  }
+  for (int64_t e = 0; e < n_edges; ++e) {
+    if (chk[e] < 0 || chk[e] >= M || var[e] < 0 || var[e] >= N)
+      return fail(LDPC_ERR_INDEX_RANGE, "edge " + std::to_string(e) + " out of range");
+    key[(size_t)e] = (int64_t)chk[e] * N + var[e];
+  }
+  std::sort(key.begin(), key.end());
+  for (size_t e = 1; e < key.size(); ++e)
+    if (key[e] == key[e - 1])
+      return fail(LDPC_ERR_DUPLICATE_EDGE, "edge (" + std::to_string(key[e] / N) + ", " +
+                                               std::to_string(key[e] % N) + ") listed twice");
+  ldpc_code_t* c = new (std::nothrow) ldpc_code_t();
+  if (!c) return fail(LDPC_ERR_NOMEM, "host allocation");
+  const int32_t E = (int32_t)n_edges;
+  c->M = M; c->N = N; c->E = E; c->K = k_info; c->Z = Z;
+  try {
+    c->cn_ptr.assign((size_t)M + 1, 0);
+    c->vn_ptr.assign((size_t)N + 1, 0);
+    c->e_vn.resize(E);
+    c->e_cn.resize(E);
+    c->vn_e.resize(E);
+    c->punct.assign((size_t)N, 0);
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return fail(LDPC_ERR_NOMEM, "host allocation");
+  }
+  for (int32_t e = 0; e < E; ++e) {
+    const int32_t m = (int32_t)(key[e] / N), n = (int32_t)(key[e] % N);
+    c->e_cn[e] = m;
+    c->e_vn[e] = n;
+    c->cn_ptr[m + 1]++;
+    c->vn_ptr[n + 1]++;
+  }
+  for (int32_t m = 0; m < M; ++m) {
+    if (c->cn_ptr[m + 1] == 0) {
+      delete c;
+      return fail(LDPC_ERR_EMPTY_NODE, "check " + std::to_string(m) + " has no edge");
+    }
+    c->dc_max = std::max(c->dc_max, c->cn_ptr[m + 1]);
+    c->cn_ptr[m + 1] += c->cn_ptr[m];
+  }
+  for (int32_t n = 0; n < N; ++n) {
+    if (c->vn_ptr[n + 1] == 0) {
+      delete c;
+      return fail(LDPC_ERR_EMPTY_NODE, "variable " + std::to_string(n) + " has no edge");
+    }
+    c->dv_max = std::max(c->dv_max, c->vn_ptr[n + 1]);
+    c->vn_ptr[n + 1] += c->vn_ptr[n];
+  }
+  std::vector<int32_t> fill((size_t)N, 0);
+  for (int32_t e = 0; e < E; ++e) {  // ascending e = ascending check within a VN
+    const int32_t n = c->e_vn[e];
+    c->vn_e[c->vn_ptr[n] + fill[n]++] = e;
+  }
+  for (int32_t n = 0; n < N; ++n) {
+    int32_t r = 0;
+    for (int32_t k = c->vn_ptr[n]; k < c->vn_ptr[n + 1]; ++k) {
+      const int32_t m = c->e_cn[c->vn_e[k]];
+      r += c->cn_ptr[m + 1] - c->cn_ptr[m];
+    }
+    c->maxr = std::max(c->maxr, r);
+    if (punct && punct[n]) {
+      c->punct[n] = 1;
+      c->n_punct++;
+    }
+  }
+  *out = c;
+  return LDPC_OK;
+}
+
+ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::DevCode** out, const uint8_t** punct) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->dev.find(dev);
+  if (it == c->dev.end()) {
+    DevCopy d;
+    const size_t words = (size_t)(c->M + 1) + 3 * (size_t)c->E + (size_t)(c->N + 1);
+    e = cudaMalloc(&d.buf, words * sizeof(int32_t));
+    if (e != cudaSuccess) return fail(LDPC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMalloc(&d.punct, (size_t)c->N);
+    if (e != cudaSuccess) {
+      cudaFree(d.buf);
+      return fail(LDPC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    std::vector<int32_t> host;
+    host.reserve(words);
+    host.insert(host.end(), c->cn_ptr.begin(), c->cn_ptr.end());
+    host.insert(host.end(), c->e_vn.begin(), c->e_vn.end());
+    host.insert(host.end(), c->e_cn.begin(), c->e_cn.end());
+    host.insert(host.end(), c->vn_ptr.begin(), c->vn_ptr.end());
+    host.insert(host.end(), c->vn_e.begin(), c->vn_e.end());
+    e = cudaMemcpy(d.buf, host.data(), words * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d.punct, c->punct.data(), (size_t)c->N, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d.buf);
+      cudaFree(d.punct);
+      return cuda_fail(e, "cudaMemcpy(code)");
+    }
+    ldpc::DevCode& g = d.g;
+    g.M = c->M; g.N = c->N; g.E = c->E;
+    g.dv_max = c->dv_max; g.dc_max = c->dc_max; g.maxr = c->maxr;
+    int32_t* p = d.buf;
+    g.cn_ptr = p; p += c->M + 1;
+    g.e_vn = p; p += c->E;
+    g.e_cn = p; p += c->E;
+    g.vn_ptr = p; p += c->N + 1;
+    g.vn_e = p;
+    it = c->dev.emplace(dev, d).first;
+  }
+  *out = &it->second.g;
+  if (punct) *punct = it->second.punct;
+  return LDPC_OK;
+}
+
+int max_optin_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ldpc_status_string(ldpc_status_t s) {
+  switch (s) {
+    case LDPC_OK: return "LDPC_OK";
+    case LDPC_ERR_INVALID_ARG: return "LDPC_ERR_INVALID_ARG";
+    case LDPC_ERR_DUPLICATE_EDGE: return "LDPC_ERR_DUPLICATE_EDGE";
+    case LDPC_ERR_INDEX_RANGE: return "LDPC_ERR_INDEX_RANGE";
+    case LDPC_ERR_EMPTY_NODE: return "LDPC_ERR_EMPTY_NODE";
+    case LDPC_ERR_UNSUPPORTED: return "LDPC_ERR_UNSUPPORTED";
+    case LDPC_ERR_CUDA: return "LDPC_ERR_CUDA";
+    case LDPC_ERR_NOMEM: return "LDPC_ERR_NOMEM";
+    case LDPC_ERR_TIMEOUT: return "LDPC_ERR_TIMEOUT";
+    case LDPC_ERR_NONFINITE_LLR: return "LDPC_ERR_NONFINITE_LLR";
+    default: return "LDPC_ERR_UNKNOWN";
+  }
+}
+
+const char* ldpc_last_error_detail(void) { return g_detail.c_str(); }
+
+ldpc_status_t ldpc_default_params(ldpc_decode_params_t* p) {
+  if (!p) return fail(LDPC_ERR_INVALID_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->schedule = LDPC_LMD_CIRBP;
+  p->arith = LDPC_FP32_SUMPRODUCT;
+  p->gamma = 0.1;
+  p->n_p = 16;
+  p->n_g = 16;
+  p->max_updates = 0;
+  p->check_interval = 1;
+  p->llr_clip = 25.0f;
+  p->q_step = 0.5f;
+  p->form = LDPC_FORM_AUTO;
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_code_create(const int32_t* check_idx, const int32_t* var_idx, int64_t n_edges,
+                               int32_t n_checks, int32_t n_vars, const uint8_t* punctured, int32_t k_info,
+                               ldpc_code_t** out) {
+  return build_code(check_idx, var_idx, n_edges, n_checks, n_vars, punctured, k_info, 0, out);
+}
+
+ldpc_status_t ldpc_code_build_qc(const int32_t* base, int32_t rows, int32_t cols, int32_t Z,
+                                 const uint8_t* punct_cols, int32_t k_info, ldpc_code_t** out) {
+  if (!out) return fail(LDPC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!base || rows <= 0 || cols <= 0 || Z <= 0) return fail(LDPC_ERR_INVALID_ARG, "bad protograph");
+  if ((int64_t)rows * Z > 0x7fffffff || (int64_t)cols * Z > 0x7fffffff)
+    return fail(LDPC_ERR_UNSUPPORTED, "lifted code too large");
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < (int64_t)rows * cols; ++i) {
+    if (base[i] >= Z || base[i] < -1) return fail(LDPC_ERR_INVALID_ARG, "shift out of [-1, Z)");
+    nnz += base[i] >= 0;
+  }
+  std::vector<int32_t> chk, var;
+  std::vector<uint8_t> punct((size_t)cols * Z, 0);
+  try {
+    chk.reserve((size_t)(nnz * Z));
+    var.reserve((size_t)(nnz * Z));
+  } catch (const std::bad_alloc&) {
+    return fail(LDPC_ERR_NOMEM, "host allocation");
+  }
+  // circulant block (r, c, s): row z of the block has its one in column (z + s) mod Z
+  for (int32_t r = 0; r < rows; ++r)
+    for (int32_t c = 0; c < cols; ++c) {
+      const int32_t s = base[(int64_t)r * cols + c];
+      if (s < 0) continue;
+      for (int32_t z = 0; z < Z; ++z) {
+        chk.push_back(r * Z + z);
+        var.push_back(c * Z + (z + s) % Z);
+      }
+    }
+  if (punct_cols)
+    for (int32_t c = 0; c < cols; ++c)
+      if (punct_cols[c]) std::fill(punct.begin() + (size_t)c * Z, punct.begin() + (size_t)(c + 1) * Z, 1);
+  return build_code(chk.data(), var.data(), (int64_t)chk.size(), rows * Z, cols * Z, punct.data(), k_info, Z,
+                    out);
+}
+
+ldpc_status_t ldpc_code_destroy(ldpc_code_t* code) {
+  if (!code) return LDPC_OK;
+  for (auto& kv : code->dev) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(kv.first);
+    cudaFree(kv.second.buf);
+    cudaFree(kv.second.punct);
+    cudaSetDevice(cur);
+  }
+  delete code;
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_code_info(const ldpc_code_t* c, ldpc_code_info_t* out) {
+  if (!c || !out) return fail(LDPC_ERR_INVALID_ARG, "NULL argument");
+  out->n_checks = c->M;
+  out->n_vars = c->N;
+  out->n_edges = c->E;
+  out->k_info = c->K;
+  out->n_punctured = c->n_punct;
+  out->max_vn_degree = c->dv_max;
+  out->max_cn_degree = c->dc_max;
+  out->max_two_hop = c->maxr;
+  out->qc_lifting = c->Z;
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_code_edges(const ldpc_code_t* c, int32_t* check_out, int32_t* var_out) {
+  if (!c || !check_out || !var_out) return fail(LDPC_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(check_out, c->e_cn.data(), sizeof(int32_t) * (size_t)c->E);
+  std::memcpy(var_out, c->e_vn.data(), sizeof(int32_t) * (size_t)c->E);
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_awgn_llr(const ldpc_code_t* code, const float* ebn0_db, int64_t batch, uint64_t seed,
+                            uint64_t frame_offset, float* llr, int8_t* qllr, float q_step, void* cuda_stream) {
+  if (!code) return fail(LDPC_ERR_INVALID_ARG, "code is NULL");
+  if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
+  if (batch == 0) return LDPC_OK;
+  if (!ebn0_db || !llr) return fail(LDPC_ERR_INVALID_ARG, "ebn0_db and llr are required");
+  if (qllr && !(q_step > 0.0f && std::isfinite(q_step))) return fail(LDPC_ERR_INVALID_ARG, "q_step must be > 0");
+  const ldpc::DevCode* g;
+  const uint8_t* punct;
+  ldpc_status_t st = ensure_device(const_cast<ldpc_code_t*>(code), &g, &punct);
+  if (st) return st;
+  const int32_t ntx = code->N - code->n_punct;
+  if (ntx <= 0) return fail(LDPC_ERR_INVALID_ARG, "every VN is punctured");
+  const float rate = (float)code->K / (float)ntx;
+  cudaError_t e = ldpc::launch_channel(*g, punct, rate, ebn0_db, batch, seed, frame_offset, llr, qllr,
+                                       q_step, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "channel launch");
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batch,
+                          const ldpc_decode_params_t* p, uint8_t* hard, int64_t* updates, uint8_t* converged,
+                          int32_t* trace, float* llr_out, void* cuda_stream) {
+  if (!code || !p) return fail(LDPC_ERR_INVALID_ARG, "code and params are required");
+  if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
+  if (p->schedule < LDPC_FLOODING || p->schedule > LDPC_ME_LMD_CIRBP)
+    return fail(LDPC_ERR_INVALID_ARG, "unknown schedule");
+  if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
+    return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
+  if (p->max_updates < 0 || p->check_interval < 0) return fail(LDPC_ERR_INVALID_ARG, "negative budget");
+  if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail(LDPC_ERR_INVALID_ARG, "gamma outside [0, 1]");
+  if (!(p->llr_clip > 0.0f && std::isfinite(p->llr_clip))) return fail(LDPC_ERR_INVALID_ARG, "llr_clip");
+  if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
+    return fail(LDPC_ERR_INVALID_ARG, "q_step");
+  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 1024))
+    return fail(LDPC_ERR_INVALID_ARG, "n_p > 0 and 0 < n_g <= 1024 required");
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || p->reserved != 0)
+    return fail(LDPC_ERR_INVALID_ARG, "bad form / reserved");
+  if (batch == 0) return LDPC_OK;
+  if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
+
+  const ldpc::DevCode* g;
+  ldpc_status_t st = ensure_device(const_cast<ldpc_code_t*>(code), &g, nullptr);
+  if (st) return st;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint32_t* status;
+  st = device_status_word(dev, &status);
+  if (st) return st;
+
+  ldpc::DecodeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = *g;
+  a.llr = llr;
+  a.batch = batch;
+  a.hard = hard;
+  a.updates = updates;
+  a.converged = converged;
+  a.trace = trace;
+  a.llr_out = llr_out;
+  a.max_updates = p->max_updates;
+  a.check_interval = p->check_interval;
+  a.gamma_f = (float)p->gamma;
+  a.gamma_i = (int32_t)std::round(p->gamma * 65534.0);
+  a.llr_clip = p->llr_clip;
+  a.n_p = p->n_p;
+  a.n_g = p->n_g;
+  a.seed = p->seed;
+  a.frame_offset = p->frame_offset;
+  a.status = status;
+  if (p->arith == LDPC_INT6_MINSUM)
+    for (int q = -127; q <= 127; ++q)
+      a.ci_table[q + 127] = (int16_t)std::round(32767.0 * std::tanh(q * (double)p->q_step / 2.0));
+
+  const int arith = p->arith == LDPC_INT6_MINSUM ? ldpc::kINT6 : ldpc::kFP32;
+  const int optin = max_optin_smem();
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e;
+  if (p->form == LDPC_FORM_GLOBAL)
+    return fail(LDPC_ERR_UNSUPPORTED, "global-memory form not available for this schedule");
+  if (p->schedule == LDPC_FLOODING) {
+    const size_t per = ldpc::flood_smem_per_frame(arith, *g);
+    if ((int)per > optin) return fail(LDPC_ERR_UNSUPPORTED, "code too large for the flooding kernel");
+    a.smem_per_frame = (int32_t)per;
+    a.frames_per_cta = 1;
+    e = ldpc::launch_flood(a, arith, s);
+  } else if (p->schedule <= LDPC_LMD_CIRBP) {
+    if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
+    if (g->maxr >= 32768) return fail(LDPC_ERR_UNSUPPORTED, "two-hop neighbourhood too large");
+    const size_t per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
+    if ((int)per > optin) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+    int fpc = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t)(optin / 2) / per));
+    if ((int64_t)fpc > batch) fpc = (int)batch;
+    a.smem_per_frame = (int32_t)per;
+    a.frames_per_cta = fpc;
+    e = ldpc::launch_se(a, arith, p->schedule, s);
+  } else {
+    const size_t per = ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g);
+    // 1 KB of headroom for the kernel's static shared table
+    if (per == 0 || (int)per + 1024 > optin)
+      return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory (or check degree > 32)");
+    a.smem_per_frame = (int32_t)per;
+    a.frames_per_cta = 1;
+    e = ldpc::launch_me(a, arith, p->schedule, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_sync(void* cuda_stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint32_t* status;
+  ldpc_status_t st = device_status_word(dev, &status);
+  if (st) return st;
+  uint32_t v = 0;
+  e = cudaMemcpy(&v, status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  if (v) {
+    e = cudaMemset(status, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  }
+  if (v & 2u) return fail(LDPC_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (v & 1u) return fail(LDPC_ERR_NONFINITE_LLR, "a decode saw a non-finite or out-of-range LLR");
+  return LDPC_OK;
+}
+
+}  // extern "C"

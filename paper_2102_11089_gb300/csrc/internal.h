@@ -1,0 +1,120 @@
+// internal.h -- structures shared by the host dispatcher and the CUDA kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ldpc {
+
+constexpr int kFP32 = 0;
+constexpr int kINT6 = 1;
+
+constexpr int kFlooding = 0;
+constexpr int kRBP = 1;
+constexpr int kCIRBP = 2;
+constexpr int kLMD = 3;
+constexpr int kMECIRBP = 4;
+constexpr int kMELMD = 5;
+
+// Tanner graph in device memory (canonical CSR edge order: by check, then variable).
+struct DevCode {
+  int32_t M, N, E;
+  int32_t dv_max, dc_max, maxr;  // maxr = max_n sum_{m in M(n)} |N(m)|
+  const int32_t* cn_ptr;         // M+1: edges of check m are [cn_ptr[m], cn_ptr[m+1])
+  const int32_t* e_vn;           // E  : variable node of edge e
+  const int32_t* e_cn;           // E  : check node of edge e
+  const int32_t* vn_ptr;         // N+1
+  const int32_t* vn_e;           // E  : edges of variable n, ascending check index
+};
+
+// Everything a decode kernel needs, passed by value.
+struct DecodeArgs {
+  DevCode g;
+  const void* llr;  // [batch][N] float (FP32) or int8 (INT6)
+  int64_t batch;
+  uint8_t* hard;
+  int64_t* updates;
+  uint8_t* converged;
+  int32_t* trace;
+  float* llr_out;
+  int64_t max_updates;
+  int64_t check_interval;
+  float gamma_f;    // FP32 threshold on D
+  int32_t gamma_i;  // INT6 threshold: round(gamma * 65534)
+  float llr_clip;
+  int32_t n_p, n_g;
+  uint64_t seed;
+  uint64_t frame_offset;
+  uint32_t* status;       // device status word (bit 0: bad input seen)
+  void* gstate;           // global-memory frame state (LDPC_FORM_GLOBAL), else null
+  int64_t gstate_stride;  // bytes per frame of gstate
+  int32_t frames_per_cta;
+  int32_t smem_per_frame;
+  int16_t ci_table[256];  // INT6: round(32767 tanh(q * q_step / 2)), q = -127..127
+};
+
+inline __host__ __device__ int align16(int x) { return (x + 15) & ~15; }
+
+// Per-frame state layout of the single-edge (warp per frame) decoder.
+struct SELayout {
+  int C, P, lam, L, Lt, D, Rmax, Ridx, par, fe, fs, fj, scr, tab, total;
+};
+
+inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, int maxr, bool need_r) {
+  const int msg = arith == kINT6 ? 1 : 4;
+  const int llr = arith == kINT6 ? 2 : 4;
+  const int dv = arith == kINT6 ? 2 : 4;
+  SELayout l;
+  int o = 0;
+  l.C = o; o = align16(o + E * msg);
+  l.P = o; o = align16(o + E * msg);
+  l.lam = o; o = align16(o + N * llr);
+  l.L = o; o = align16(o + N * llr);
+  l.Lt = o; o = align16(o + N * llr);
+  l.D = o; o = align16(o + N * dv);
+  l.Rmax = o; o = align16(o + (need_r ? M * msg : 0));
+  l.Ridx = o; o = align16(o + (need_r ? M * 4 : 0));
+  l.par = o; o = align16(o + ((M + 31) / 32) * 4);
+  l.fe = o; o = align16(o + maxr * 4);
+  l.fs = o; o = align16(o + maxr * 4);
+  l.fj = o; o = align16(o + maxr * 4);
+  l.scr = o; o = align16(o + maxr * 4);
+  l.tab = o; o = align16(o + (arith == kINT6 ? 256 * 2 : 0));
+  l.total = o;
+  return l;
+}
+
+// Per-frame state layout of the flooding (CTA per frame) decoder.
+struct FloodLayout {
+  int C, S, lam, L, tab, total;
+};
+
+inline __host__ __device__ FloodLayout flood_layout(int arith, int N, int E) {
+  const int msg = arith == kINT6 ? 1 : 4;
+  const int llr = arith == kINT6 ? 2 : 4;
+  FloodLayout l;
+  int o = 0;
+  l.C = o; o = align16(o + E * msg);
+  l.S = o; o = align16(o + E * 4);
+  l.lam = o; o = align16(o + N * llr);
+  l.L = o; o = align16(o + N * llr);
+  l.tab = o; o = align16(o + 0);
+  l.total = o;
+  return l;
+}
+
+// Launchers (return a cudaError_t from the launch).
+cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
+cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s);
+cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
+cudaError_t launch_channel(const DevCode& g, const uint8_t* punct, float rate, const float* ebn0,
+                           int64_t batch, uint64_t seed, uint64_t frame_offset, float* llr,
+                           int8_t* qllr, float q_step, cudaStream_t s);
+
+size_t se_smem_per_frame(int arith, int sched, const DevCode& g);
+size_t flood_smem_per_frame(int arith, const DevCode& g);
+size_t me_smem_per_frame(int arith, int sched, const DevCode& g, int n_p, int n_g);
+
+}  // namespace ldpc
