@@ -290,12 +290,12 @@ def run_ours(args):
             e1.record(stream)
             dec_ev.append((e0, e1))
 
+    clocks = Clocks()  # sampler started before the warm-up: its start-up must not overlap timing
+    clocks.start()
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
     L.sync(stream)
-    clocks = Clocks()
-    clocks.start()
     upd_total = 0
     barrier(world, device)
     torch.cuda.synchronize()

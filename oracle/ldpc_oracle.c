@@ -28,7 +28,8 @@
  *  R5  "In parallel" (Algorithms 5, 6) is a two-phase step: all selections on
  *      the pre-step state, all commits, then one refresh of everything touched.
  *  R6  Algorithm 4's random choice takes the members of the fill group with the
- *      smallest Philox4x32-10 keys (key = seed, counter = (n, step, frame)).
+ *      smallest keys (key of n = word n mod 4 of Philox4x32-10 with key = seed,
+ *      counter = (n / 4, step, frame)); equal keys go to the lower index.
  *  R7  Degree-1 rule (Sec. 5.A): if d_v(n*) = 1 the LMD candidate set is
  *      N(m*)\n*; if the candidate set is still empty, the global argmax of D.
  *  R8  Syndrome checked at update count 0 and whenever the count crosses a
@@ -178,12 +179,14 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-static uint32_t philox_word0(uint32_t a, uint32_t b, uint64_t frame, uint64_t seed) {
-    uint32_t ctr[4] = {a, b, (uint32_t)frame, (uint32_t)(frame >> 32)};
+/* Random key of variable n for Algorithm 4's fill at a given step: word     */
+/* (n mod 4) of Philox4x32-10 with counter (n / 4, step, frame), key = seed.  */
+static uint32_t fill_key(uint32_t n, uint32_t step, uint64_t frame, uint64_t seed) {
+    uint32_t ctr[4] = {n / 4u, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t o[4];
     orc_philox4x32_10(ctr, key, o);
-    return o[0];
+    return o[n % 4u];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -520,7 +523,7 @@ static int alg4(fr_t *f, const int *inS, int np, int *out, double *margin) {
         kn_t *c = (kn_t *)malloc(sizeof(kn_t) * (size_t)cnt[fill]);
         for (int n = 0; n < g->N; n++)
             if (grp[n] == fill) {
-                c[nc].key = philox_word0((uint32_t)n, (uint32_t)f->step, f->frame, f->pr->seed);
+                c[nc].key = fill_key((uint32_t)n, (uint32_t)f->step, f->frame, f->pr->seed);
                 c[nc].n = n;
                 nc++;
             }

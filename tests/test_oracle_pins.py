@@ -449,8 +449,8 @@ def test_alg4_hand_cases():
     assert list(P) == [0, 1, 3, 4]
     # k* = 0: random fill of one element of the top group {0, 1}
     P, _ = oracle.alg4(D, allS, n_g=4, n_p=1, seed=7, frame=3, step=5)
-    k0 = oracle.philox4x32_10([0, 5, 3, 0], [7, 0])[0]
-    k1 = oracle.philox4x32_10([1, 5, 3, 0], [7, 0])[0]
+    w = oracle.philox4x32_10([0, 5, 3, 0], [7, 0])  # VNs 0..3 share counter (0, step, frame)
+    k0, k1 = w[0], w[1]
     assert list(P) == [0 if (k0, 0) < (k1, 1) else 1]
     # |S| <= N_P: everything is selected
     S = np.array([1, 0, 1, 0, 0], np.uint8)
