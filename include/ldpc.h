@@ -80,7 +80,9 @@ typedef struct {
     int32_t max_vn_degree; /* max |M(n)|                                         */
     int32_t max_cn_degree; /* max |N(m)|                                         */
     int32_t max_two_hop;   /* max over n of sum_{m in M(n)} |N(m)|               */
-    int32_t qc_lifting;    /* Z for codes built by ldpc_code_build_qc, else 0    */
+    int32_t qc_lifting;    /* Z when kernels use the protograph view of a code
+                              built by ldpc_code_build_qc (graph neighbours computed
+                              from the circulant shifts), else 0                  */
 } ldpc_code_info_t;
 
 typedef struct {

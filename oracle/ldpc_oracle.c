@@ -356,7 +356,12 @@ static void am_push(amax_t *a, int idx, double v) {
         a->second = v;
     }
 }
-static double am_gap(const amax_t *a) { return a->second == -INFINITY ? INFINITY : a->best - a->second; }
+/* top-2 gap relative to max(1, |best|): residuals scale with message          */
+/* magnitudes (up to llr_clip), CI values lie in [0, 1) and keep an absolute gap */
+static double am_gap(const amax_t *a) {
+    if (a->second == -INFINITY) return INFINITY;
+    return (a->best - a->second) / fmax(1.0, fabs(a->best));
+}
 static void am_count(fr_t *f, const amax_t *a) { if (a->ncand > 0) f->ctr[CT_CMP] += a->ncand - 1; }
 
 /* argmax over D of all VNs (Alg. 1 line 4, Alg. 3 line 4)                    */

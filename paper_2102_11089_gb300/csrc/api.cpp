@@ -28,9 +28,9 @@ ldpc_status_t cuda_fail(cudaError_t e, const char* where) {
 }
 
 struct DevCopy {
-  int32_t* buf = nullptr;  // cn_ptr | e_vn | e_cn | vn_ptr | vn_e
+  int32_t* buf = nullptr;  // tab blob, then the QC blob (if any)
   uint8_t* punct = nullptr;
-  ldpc::DevCode g{};
+  ldpc::GraphDesc g{};
 };
 
 std::mutex g_status_mu;
@@ -60,6 +60,10 @@ struct ldpc_code {
   int32_t dv_max = 0, dc_max = 0, maxr = 0, n_punct = 0;
   std::vector<int32_t> cn_ptr, e_vn, e_cn, vn_ptr, vn_e;
   std::vector<uint8_t> punct;
+  // protograph view (codes from ldpc_code_build_qc): see graph.cuh
+  std::vector<int32_t> qc;  // rowbase | rowfirst | colfirst | rowblk | colblk
+  int32_t qc_R = 0, qc_C = 0, qc_nnz = 0;
+  uint32_t qc_zmul = 0, qc_zshift = 0;
   std::mutex mu;
   std::map<int, DevCopy> dev;
 };
@@ -150,7 +154,7 @@ ldpc_status_t build_code(const int32_t* chk, const int32_t* var, int64_t n_edges
   return LDPC_OK;
 }
 
-ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::DevCode** out, const uint8_t** punct) {
+ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::GraphDesc** out, const uint8_t** punct) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -158,7 +162,8 @@ ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::DevCode** out, const uin
   auto it = c->dev.find(dev);
   if (it == c->dev.end()) {
     DevCopy d;
-    const size_t words = (size_t)(c->M + 1) + 3 * (size_t)c->E + (size_t)(c->N + 1);
+    const size_t tab_words = (size_t)(c->M + 1) + 3 * (size_t)c->E + (size_t)(c->N + 1);
+    const size_t words = tab_words + c->qc.size();
     e = cudaMalloc(&d.buf, words * sizeof(int32_t));
     if (e != cudaSuccess) return fail(LDPC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     e = cudaMalloc(&d.punct, (size_t)c->N);
@@ -173,6 +178,7 @@ ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::DevCode** out, const uin
     host.insert(host.end(), c->e_cn.begin(), c->e_cn.end());
     host.insert(host.end(), c->vn_ptr.begin(), c->vn_ptr.end());
     host.insert(host.end(), c->vn_e.begin(), c->vn_e.end());
+    host.insert(host.end(), c->qc.begin(), c->qc.end());
     e = cudaMemcpy(d.buf, host.data(), words * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d.punct, c->punct.data(), (size_t)c->N, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -180,20 +186,107 @@ ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::DevCode** out, const uin
       cudaFree(d.punct);
       return cuda_fail(e, "cudaMemcpy(code)");
     }
-    ldpc::DevCode& g = d.g;
+    ldpc::GraphDesc& g = d.g;
+    std::memset(&g, 0, sizeof(g));
     g.M = c->M; g.N = c->N; g.E = c->E;
     g.dv_max = c->dv_max; g.dc_max = c->dc_max; g.maxr = c->maxr;
-    int32_t* p = d.buf;
-    g.cn_ptr = p; p += c->M + 1;
-    g.e_vn = p; p += c->E;
-    g.e_cn = p; p += c->E;
-    g.vn_ptr = p; p += c->N + 1;
-    g.vn_e = p;
+    g.tab = d.buf;
+    g.tab_words = (int32_t)tab_words;
+    g.tab_in_smem = tab_words * 4 <= 32 * 1024;
+    if (!c->qc.empty()) {
+      g.is_qc = 1;
+      g.qc = d.buf + tab_words;
+      g.qc_words = (int32_t)c->qc.size();
+      g.qc_R = c->qc_R; g.qc_C = c->qc_C; g.qc_Z = c->Z; g.qc_nnz = c->qc_nnz;
+      g.qc_zmul = c->qc_zmul; g.qc_zshift = c->qc_zshift;
+    }
     it = c->dev.emplace(dev, d).first;
   }
   *out = &it->second.g;
   if (punct) *punct = it->second.punct;
   return LDPC_OK;
+}
+
+// Protograph view of a lifted code (layout in graph.cuh), kept only when it
+// reproduces the CSR maps exactly and fits the packed fields.
+void build_qc_view(ldpc_code_t* c, const int32_t* base, int32_t R, int32_t Cc, int32_t Z) {
+  c->qc.clear();
+  if (R > 255 || Z > 65535 || Z <= 0) return;
+  std::vector<int32_t> rowfirst(R + 1, 0), colfirst(Cc + 1, 0), rowbase(R + 1, 0);
+  std::vector<uint32_t> rowblk, colblk;
+  std::vector<int32_t> kpos((size_t)R * Cc, -1);
+  for (int32_t r = 0; r < R; ++r) {
+    rowfirst[r] = (int32_t)rowblk.size();
+    int32_t k = 0;
+    for (int32_t col = 0; col < Cc; ++col) {
+      const int32_t sft = base[(int64_t)r * Cc + col];
+      if (sft < 0) continue;
+      rowblk.push_back(((uint32_t)col << 16) | (uint32_t)sft);
+      kpos[(size_t)r * Cc + col] = k++;
+    }
+    if (k > 255) return;
+    rowbase[r + 1] = rowbase[r] + k * Z;
+  }
+  rowfirst[R] = (int32_t)rowblk.size();
+  for (int32_t col = 0; col < Cc; ++col) {
+    colfirst[col] = (int32_t)colblk.size();
+    for (int32_t r = 0; r < R; ++r) {
+      const int32_t sft = base[(int64_t)r * Cc + col];
+      if (sft < 0) continue;
+      colblk.push_back(((uint32_t)r << 24) | ((uint32_t)kpos[(size_t)r * Cc + col] << 16) | (uint32_t)sft);
+    }
+  }
+  colfirst[Cc] = (int32_t)colblk.size();
+  // n / Z == umulhi(n, mul) >> shift for every n < max(R, C) Z
+  const uint32_t limit = (uint32_t)std::max(R, Cc) * (uint32_t)Z;
+  uint32_t mul = 0, shift = 0;
+  bool found = false;
+  for (uint32_t sh = 0; sh < 32 && !found; ++sh) {
+    const unsigned __int128 num = ((unsigned __int128)1) << (32 + sh);
+    const unsigned __int128 m = (num + Z - 1) / Z;
+    if (m >> 32) continue;
+    bool ok = true;
+    for (uint32_t n = 0; n < limit && ok; ++n)
+      ok = (uint32_t)((((uint64_t)n * (uint64_t)m) >> 32) >> sh) == n / (uint32_t)Z;
+    if (ok) {
+      mul = (uint32_t)m;
+      shift = sh;
+      found = true;
+    }
+  }
+  if (!found) return;
+  // self-check: the view must give the CSR edge ids and neighbours
+  for (int32_t m = 0; m < c->M; ++m) {
+    const int32_t r = m / Z, z = m % Z, dc = rowfirst[r + 1] - rowfirst[r];
+    if (c->cn_ptr[m] != rowbase[r] + z * dc || c->cn_ptr[m + 1] - c->cn_ptr[m] != dc) return;
+    for (int32_t k = 0; k < dc; ++k) {
+      const uint32_t blk = rowblk[rowfirst[r] + k];
+      const int32_t n = (int32_t)(blk >> 16) * Z + (z + (int32_t)(blk & 0xffffu)) % Z;
+      if (c->e_vn[c->cn_ptr[m] + k] != n) return;
+    }
+  }
+  for (int32_t n = 0; n < c->N; ++n) {
+    const int32_t col = n / Z, z = n % Z, dv = colfirst[col + 1] - colfirst[col];
+    if (c->vn_ptr[n + 1] - c->vn_ptr[n] != dv) return;
+    for (int32_t k = 0; k < dv; ++k) {
+      const uint32_t blk = colblk[colfirst[col] + k];
+      const int32_t r = (int32_t)(blk >> 24), kk = (int32_t)((blk >> 16) & 255u), sft = (int32_t)(blk & 0xffffu);
+      const int32_t zz = ((z - sft) % Z + Z) % Z;
+      const int32_t dc = rowfirst[r + 1] - rowfirst[r];
+      const int32_t e = rowbase[r] + zz * dc + kk;
+      if (c->vn_e[c->vn_ptr[n] + k] != e || c->e_cn[e] != r * Z + zz) return;
+    }
+  }
+  c->qc.insert(c->qc.end(), rowbase.begin(), rowbase.end());
+  c->qc.insert(c->qc.end(), rowfirst.begin(), rowfirst.end());
+  c->qc.insert(c->qc.end(), colfirst.begin(), colfirst.end());
+  for (uint32_t v : rowblk) c->qc.push_back((int32_t)v);
+  for (uint32_t v : colblk) c->qc.push_back((int32_t)v);
+  c->qc_R = R;
+  c->qc_C = Cc;
+  c->qc_nnz = (int32_t)rowblk.size();
+  c->qc_zmul = mul;
+  c->qc_zshift = shift;
 }
 
 int max_optin_smem() {
@@ -280,8 +373,10 @@ ldpc_status_t ldpc_code_build_qc(const int32_t* base, int32_t rows, int32_t cols
   if (punct_cols)
     for (int32_t c = 0; c < cols; ++c)
       if (punct_cols[c]) std::fill(punct.begin() + (size_t)c * Z, punct.begin() + (size_t)(c + 1) * Z, 1);
-  return build_code(chk.data(), var.data(), (int64_t)chk.size(), rows * Z, cols * Z, punct.data(), k_info, Z,
-                    out);
+  ldpc_status_t st = build_code(chk.data(), var.data(), (int64_t)chk.size(), rows * Z, cols * Z, punct.data(),
+                                k_info, Z, out);
+  if (st == LDPC_OK) build_qc_view(*out, base, rows, cols, Z);
+  return st;
 }
 
 ldpc_status_t ldpc_code_destroy(ldpc_code_t* code) {
@@ -308,7 +403,7 @@ ldpc_status_t ldpc_code_info(const ldpc_code_t* c, ldpc_code_info_t* out) {
   out->max_vn_degree = c->dv_max;
   out->max_cn_degree = c->dc_max;
   out->max_two_hop = c->maxr;
-  out->qc_lifting = c->Z;
+  out->qc_lifting = c->qc.empty() ? 0 : c->Z;
   return LDPC_OK;
 }
 
@@ -326,15 +421,15 @@ ldpc_status_t ldpc_awgn_llr(const ldpc_code_t* code, const float* ebn0_db, int64
   if (batch == 0) return LDPC_OK;
   if (!ebn0_db || !llr) return fail(LDPC_ERR_INVALID_ARG, "ebn0_db and llr are required");
   if (qllr && !(q_step > 0.0f && std::isfinite(q_step))) return fail(LDPC_ERR_INVALID_ARG, "q_step must be > 0");
-  const ldpc::DevCode* g;
+  const ldpc::GraphDesc* g;
   const uint8_t* punct;
   ldpc_status_t st = ensure_device(const_cast<ldpc_code_t*>(code), &g, &punct);
   if (st) return st;
   const int32_t ntx = code->N - code->n_punct;
   if (ntx <= 0) return fail(LDPC_ERR_INVALID_ARG, "every VN is punctured");
   const float rate = (float)code->K / (float)ntx;
-  cudaError_t e = ldpc::launch_channel(*g, punct, rate, ebn0_db, batch, seed, frame_offset, llr, qllr,
-                                       q_step, (cudaStream_t)cuda_stream);
+  cudaError_t e = ldpc::launch_channel(g->N, punct, rate, ebn0_db, batch, seed, frame_offset, llr, qllr, q_step,
+                                       (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "channel launch");
   return LDPC_OK;
 }
@@ -360,7 +455,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
 
-  const ldpc::DevCode* g;
+  const ldpc::GraphDesc* g;
   ldpc_status_t st = ensure_device(const_cast<ldpc_code_t*>(code), &g, nullptr);
   if (st) return st;
   int dev = 0;
@@ -389,6 +484,9 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   a.seed = p->seed;
   a.frame_offset = p->frame_offset;
   a.status = status;
+  a.graph_smem = ldpc::graph_smem_bytes(*g);
+  a.team_w = 1;
+  while (a.team_w < g->dc_max) a.team_w <<= 1;
   if (p->arith == LDPC_INT6_MINSUM)
     for (int q = -127; q <= 127; ++q)
       a.ci_table[q + 127] = (int16_t)std::round(32767.0 * std::tanh(q * (double)p->q_step / 2.0));
@@ -399,18 +497,21 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   cudaError_t e;
   if (p->form == LDPC_FORM_GLOBAL)
     return fail(LDPC_ERR_UNSUPPORTED, "global-memory form not available for this schedule");
+  if (g->dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
+  const int gsm = a.graph_smem;
   if (p->schedule == LDPC_FLOODING) {
     const size_t per = ldpc::flood_smem_per_frame(arith, *g);
-    if ((int)per > optin) return fail(LDPC_ERR_UNSUPPORTED, "code too large for the flooding kernel");
+    if ((int)per + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "code too large for the flooding kernel");
     a.smem_per_frame = (int32_t)per;
     a.frames_per_cta = 1;
     e = ldpc::launch_flood(a, arith, s);
   } else if (p->schedule <= LDPC_LMD_CIRBP) {
     if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
-    if (g->maxr >= 32768) return fail(LDPC_ERR_UNSUPPORTED, "two-hop neighbourhood too large");
     const size_t per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
-    if ((int)per > optin) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
-    int fpc = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t)(optin / 2) / per));
+    if ((int)per + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+    // frames per CTA: fill about half the opt-in shared memory so two CTAs share an SM
+    int fpc = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t)std::max(0, optin / 2 - gsm) / per));
+    while (fpc > 1 && (int)(fpc * per) + gsm > optin) --fpc;
     if ((int64_t)fpc > batch) fpc = (int)batch;
     a.smem_per_frame = (int32_t)per;
     a.frames_per_cta = fpc;
@@ -418,8 +519,9 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   } else {
     const size_t per = ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g);
     // 1 KB of headroom for the kernel's static shared table
-    if (per == 0 || (int)per + 1024 > optin)
-      return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory (or check degree > 32)");
+    if (per == 0 || (int)per + gsm + 1024 > optin)
+      return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+    if (p->n_g > 255) return fail(LDPC_ERR_UNSUPPORTED, "n_g > 255 for the multi-edge kernel");
     a.smem_per_frame = (int32_t)per;
     a.frames_per_cta = 1;
     e = ldpc::launch_me(a, arith, p->schedule, s);

@@ -81,18 +81,17 @@ __global__ void __launch_bounds__(256) awgn_kernel(int N, const uint8_t* __restr
 
 }  // namespace
 
-cudaError_t launch_channel(const DevCode& g, const uint8_t* punct, float rate, const float* ebn0,
-                           int64_t batch, uint64_t seed, uint64_t frame_offset, float* llr,
-                           int8_t* qllr, float q_step, cudaStream_t s) {
+cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float* ebn0, int64_t batch,
+                           uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
+                           cudaStream_t s) {
   if (batch == 0) return cudaSuccess;
-  const int64_t work = batch * (int64_t)((g.N + 3) / 4);
+  const int64_t work = batch * (int64_t)((N + 3) / 4);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (work + 255) / 256;
   const int grid = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-  awgn_kernel<<<grid, 256, 0, s>>>(g.N, punct, rate, ebn0, batch, seed, frame_offset, llr, qllr,
-                                   q_step);
+  awgn_kernel<<<grid, 256, 0, s>>>(N, punct, rate, ebn0, batch, seed, frame_offset, llr, qllr, q_step);
   return cudaGetLastError();
 }
 

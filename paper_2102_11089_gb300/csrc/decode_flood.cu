@@ -1,55 +1,31 @@
 // decode_flood.cu -- flooding BP (Sec. 1), one frame per CTA.
 //
 // One iteration computes every V2C message from the previous C2V messages
-// (eq. 1, written as L_n - L^C_{m->n}), then every C2V message (eq. 2 or
-// min-sum) in parallel, then the total LLRs (eq. 3); it propagates E messages
-// (the iteration unit of Sec. 2.A).  Messages, LLRs and the per-edge scratch of
-// encoded V2C values sit in shared memory; threads stride over edges, then
-// variable nodes, then checks (syndrome).
+// (eq. 1, written as L_n - L^C_{m->n}) and every C2V message from those
+// (eq. 2 or min-sum) in one pass of check teams (each edge is read and
+// rewritten by the lane that owns it, so the update is in place), then the
+// total LLRs (eq. 3).  An iteration propagates E messages (Sec. 2.A).
 #include "device_math.cuh"
 
 namespace ldpc {
 
 namespace {
 
-__device__ __forceinline__ float flood_c2v(const float* S, int e, int c0, int c1, float clip) {
-  float sum = 0.0f;
-  unsigned neg = 0;
-  for (int k = c0; k < c1; ++k) {
-    if (k == e) continue;
-    const float v = S[k];
-    sum += fabsf(v);
-    neg ^= (__float_as_uint(v) >> 31);
-  }
-  return combine_fp(sum, neg, clip);
-}
-
-__device__ __forceinline__ int8_t flood_c2v(const int8_t* S, int e, int c0, int c1, float) {
-  int mag = 31;
-  unsigned neg = 0;
-  for (int k = c0; k < c1; ++k) {
-    if (k == e) continue;
-    const int v = S[k];
-    neg ^= (v < 0);
-    mag = min(mag, abs(v));
-  }
-  return (int8_t)(neg ? -mag : mag);
-}
-
-template <int A>
+template <int A, class G>
 __global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
   const int64_t b = blockIdx.x;
-  const DevCode& g = a.g;
-  const FloodLayout ly = flood_layout(A, g.N, g.E);
-  M_* C = (M_*)(smem_raw + ly.C);
-  M_* S = (M_*)(smem_raw + ly.S);
-  L_* lam = (L_*)(smem_raw + ly.lam);
-  L_* L = (L_*)(smem_raw + ly.L);
-  const int N = g.N, E = g.E, M = g.M;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int N = a.g.N, E = a.g.E, M = a.g.M;
+  const FloodLayout ly = flood_layout(A, N, E);
+  unsigned char* base = smem_raw + a.graph_smem;
+  M_* C = (M_*)(base + ly.C);
+  L_* lam = (L_*)(base + ly.lam);
+  L_* L = (L_*)(base + ly.L);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int W = a.team_w, tpw = 32 / W, team = lane / W, r = lane % W;
   const float clip = a.llr_clip;
 
   int bad = 0;
@@ -84,9 +60,9 @@ __global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
   auto syndrome_nonzero = [&]() -> int {
     int any = 0;
     for (int m = tid; m < M; m += nt) {
-      const int c0 = __ldg(g.cn_ptr + m), c1 = __ldg(g.cn_ptr + m + 1);
+      const typename G::C cc = g.cn(m);
       unsigned p = 0;
-      for (int e = c0; e < c1; ++e) p ^= (L[__ldg(g.e_vn + e)] < (L_)0);
+      for (int k = 0; k < cc.d; ++k) p ^= (L[g.cvn(cc, k)] < (L_)0);
       any |= (int)p;
     }
     return __syncthreads_or(any);
@@ -96,23 +72,15 @@ __global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
   bool ok = a.check_interval > 0 && !syndrome_nonzero();
   while (!ok && count + E <= a.max_updates) {
     const int64_t before = count;
-    for (int e = tid; e < E; e += nt) {  // V2C from the previous C2V (eq. 1)
-      const int j = __ldg(g.e_vn + e);
-      if (A == kFP32) ((float*)S)[e] = encode_fp((float)L[j] - (float)C[e], clip);
-      else ((int8_t*)S)[e] = encode_int((int)L[j] - (int)C[e]);
+    for (int t0 = warp * tpw; t0 < M; t0 += nw * tpw) {  // every C2V from the previous V2C
+      const int m = t0 + team;
+      int e, j;
+      M_ out;
+      const int dc = team_c2v<A, G>(g, C, L, m < M ? m : -1, r, W, clip, e, j, out);
+      if (r < dc) C[e] = out;
     }
     __syncthreads();
-    for (int e = tid; e < E; e += nt) {  // every C2V (eq. 2 / min-sum)
-      const int m = __ldg(g.e_cn + e);
-      C[e] = flood_c2v((const M_*)S, e, __ldg(g.cn_ptr + m), __ldg(g.cn_ptr + m + 1), clip);
-    }
-    __syncthreads();
-    for (int n = tid; n < N; n += nt) {  // total LLR (eq. 3)
-      const int v0 = __ldg(g.vn_ptr + n), v1 = __ldg(g.vn_ptr + n + 1);
-      L_ acc = lam[n];
-      for (int k = v0; k < v1; ++k) acc = (L_)(acc + C[__ldg(g.vn_e + k)]);
-      L[n] = acc;
-    }
+    for (int n = tid; n < N; n += nt) L[n] = vn_total<A, G>(g, lam, C, n);  // eq. (3)
     __syncthreads();
     count += E;
     if (a.check_interval > 0 && (count / a.check_interval) > (before / a.check_interval))
@@ -129,29 +97,25 @@ __global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
   }
 }
 
+template <int A, class G>
+cudaError_t launch_g(const DecodeArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame;
+  const int threads = a.g.E >= 4096 ? 512 : (a.g.E >= 1024 ? 256 : 128);
+  auto k = flood_decode_kernel<A, G>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k<<<(unsigned)a.batch, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t flood_smem_per_frame(int arith, const DevCode& g) {
-  return (size_t)flood_layout(arith, g.N, g.E).total;
-}
+size_t flood_smem_per_frame(int arith, const GraphDesc& g) { return (size_t)flood_layout(arith, g.N, g.E).total; }
 
 cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s) {
   if (a.batch == 0) return cudaSuccess;
-  const size_t smem = (size_t)a.smem_per_frame;
-  const int threads = a.g.E >= 4096 ? 512 : (a.g.E >= 1024 ? 256 : 128);
-  cudaError_t err;
-  if (arith == kFP32) {
-    err = cudaFuncSetAttribute(flood_decode_kernel<kFP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (err != cudaSuccess) return err;
-    flood_decode_kernel<kFP32><<<(unsigned)a.batch, threads, smem, s>>>(a);
-  } else {
-    err = cudaFuncSetAttribute(flood_decode_kernel<kINT6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (err != cudaSuccess) return err;
-    flood_decode_kernel<kINT6><<<(unsigned)a.batch, threads, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+  if (arith == kFP32) return a.g.is_qc ? launch_g<kFP32, QCGraph>(a, s) : launch_g<kFP32, TabGraph>(a, s);
+  return a.g.is_qc ? launch_g<kINT6, QCGraph>(a, s) : launch_g<kINT6, TabGraph>(a, s);
 }
 
 }  // namespace ldpc

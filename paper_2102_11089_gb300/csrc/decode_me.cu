@@ -13,17 +13,21 @@
 // degree): lane r of a team owns edge r of the check and gets the exclude-one
 // combination of eq. (2) (or min-sum) by W width-limited shuffles.
 //
-// Algorithm 4's random fill takes, from the fill group, the members with the
-// smallest Philox4x32-10 keys (key = seed, counter = (n, step, frame)); the
-// k-th smallest key is found by an exact 4 x 8-bit radix select.
+// Algorithm 4 keeps the group index floor(D N_G) of every VN in shared memory.
+// Its random fill takes the fill-group members with the smallest keys (word
+// n mod 4 of Philox4x32-10 with counter (n/4, step, frame), key = seed; equal
+// keys to the lower index): members with key <= T are gathered (T bisected
+// until between `need` and kCap of them), then ranked exactly.
 #include "device_math.cuh"
 
 namespace ldpc {
 
 namespace {
 
+constexpr int kCap = 1024;  // candidate list of the random fill
+
 struct MELayout {
-  int C, P, lam, L, Lt, D, par, key, sel, est, best, cnl, hist, cnt, bits, misc, total;
+  int C, P, lam, L, D, grp, par, sel, est, best, cnl, cand, cnt, bits, misc, total;
 };
 
 __host__ __device__ inline MELayout me_layout(int arith, int M, int N, int E, int n_p, int dvm, int n_g) {
@@ -36,18 +40,17 @@ __host__ __device__ inline MELayout me_layout(int arith, int M, int N, int E, in
   l.P = o; o = align16(o + E * msg);
   l.lam = o; o = align16(o + N * llr);
   l.L = o; o = align16(o + N * llr);
-  l.Lt = o; o = align16(o + N * llr);
   l.D = o; o = align16(o + N * dv);
+  l.grp = o; o = align16(o + N);
   l.par = o; o = align16(o + ((M + 31) / 32) * 4);
-  l.key = o; o = align16(o + N * 4);
   l.sel = o; o = align16(o + n_p * 4);
   l.est = o; o = align16(o + n_p * 4);
   l.best = o; o = align16(o + n_p * 8);
   l.cnl = o; o = align16(o + n_p * (dvm > 1 ? dvm - 1 : 1) * 8);
-  l.hist = o; o = align16(o + 256 * 4);
+  l.cand = o; o = align16(o + kCap * 8);
   l.cnt = o; o = align16(o + n_g * 4);
   l.bits = o; o = align16(o + ((N + 31) / 32) * 4);
-  l.misc = o; o = align16(o + 16 * 8);
+  l.misc = o; o = align16(o + 32 * 4);
   l.total = o;
   return l;
 }
@@ -55,14 +58,13 @@ __host__ __device__ inline MELayout me_layout(int arith, int M, int N, int E, in
 // shared scalars (misc area)
 struct MEMisc {
   int unsat;
-  int ncn;       // affected checks this step
-  int nsel;      // selected VNs
-  int npp;       // |P'| (ME-LMD)
-  int kstar, fill_g, need, take_all_eq;
-  uint32_t thr;  // radix threshold key
-  int cnt_eq;
-  int sz;
-  int pad[5];
+  int ncn;   // affected checks this step
+  int nsel;  // selected VNs
+  int npp;   // |P'| (ME-LMD)
+  int kstar, fill_g, need, sz;
+  int ncand;
+  uint32_t thr, lo, hi;
+  int done, hi_set;
 };
 
 template <int A>
@@ -74,120 +76,62 @@ struct MEState {
   M_* P;
   L_* lam;
   L_* L;
-  L_* Lt;
   D_* D;
+  uint8_t* grp;
   uint32_t* par;
-  uint32_t* key;
   int32_t* sel;
   int32_t* est;
   unsigned long long* best;
   int2* cnl;  // (check, owner k)
-  int32_t* hist;
+  unsigned long long* cand;
   int32_t* cnt;
   uint32_t* bits;  // selection bitmap over VNs
   MEMisc* misc;
-  int16_t* tab;
+  const int16_t* tab;
 };
 
-__device__ __forceinline__ uint32_t philox_word0(uint32_t n, uint32_t step, uint64_t frame, uint64_t seed) {
-  uint32_t c0 = n, c1 = step, c2 = (uint32_t)frame, c3 = (uint32_t)(frame >> 32);
+__device__ __forceinline__ void philox4(uint32_t c[4], uint64_t seed) {
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
-  return c0;
 }
 
 __device__ __forceinline__ float ci_me(const MEState<kFP32>&, float a, float b) { return ci_fp(a, b); }
-__device__ __forceinline__ uint16_t ci_me(const MEState<kINT6>& s, int a, int b) {
-  return ci_int(a, b, s.tab);
-}
+__device__ __forceinline__ uint16_t ci_me(const MEState<kINT6>& s, int a, int b) { return ci_int(a, b, s.tab); }
 
+// Algorithm 4 line 2: group i = floor(D N_G), clamped to N_G - 1
 __device__ __forceinline__ int group_of(float d, int ng) { return min((int)floorf(d * (float)ng), ng - 1); }
 __device__ __forceinline__ int group_of(uint16_t d, int ng) { return min((int)(((int)d * ng) / 65534), ng - 1); }
 
-__device__ __forceinline__ uint32_t rkey_me(float p, float c) { return mkey(fabsf(p - c)); }
-__device__ __forceinline__ uint32_t rkey_me(int8_t p, int8_t c) { return (uint32_t)abs((int)p - (int)c); }
+__device__ __forceinline__ bool in_bits(const uint32_t* bits, int n) { return (bits[n >> 5] >> (n & 31)) & 1u; }
 
-// Team C2V of check m: lane r (< W) of the team owns edge r.  V2C = L_j - C[e]
-// (eq. 1), output P[e] for every edge of the check (eq. 2 / min-sum).
+// Algorithm 4 over S = {n : bit n of s.bits clear}: sets the bits of the
+// selected VNs (at most np of them).  All threads call it.
 template <int A>
-__device__ __forceinline__ void team_c2v(const DevCode& g, const MEState<A>& s, int m, int r, int W,
-                                         float clip) {
-  const int c0 = m >= 0 ? __ldg(g.cn_ptr + m) : 0;
-  const int dc = m >= 0 ? __ldg(g.cn_ptr + m + 1) - c0 : 0;
-  const int e = c0 + r;
-  if (A == kFP32) {
-    float enc = 0.0f;
-    if (r < dc) {
-      const int j = __ldg(g.e_vn + e);
-      enc = encode_fp((float)s.L[j] - (float)s.C[e], clip);
-    }
-    float sum = 0.0f;
-    unsigned neg = 0;
-    for (int k = 0; k < W; ++k) {
-      const float v = __shfl_sync(kFull, enc, k, W);
-      if (k != r && k < dc) {
-        sum += fabsf(v);
-        neg ^= __float_as_uint(v) >> 31;
-      }
-    }
-    if (r < dc) ((float*)s.P)[e] = combine_fp(sum, neg, clip);
-  } else {
-    int enc = 0;
-    if (r < dc) {
-      const int j = __ldg(g.e_vn + e);
-      enc = encode_int((int)s.L[j] - (int)s.C[e]);
-    }
-    int mag = 31;
-    unsigned neg = 0;
-    for (int k = 0; k < W; ++k) {
-      const int v = __shfl_sync(kFull, enc, k, W);
-      if (k != r && k < dc) {
-        neg ^= (v < 0);
-        mag = min(mag, abs(v));
-      }
-    }
-    if (r < dc) ((int8_t*)s.P)[e] = (int8_t)(neg ? -mag : mag);
-  }
-}
-
-template <int A>
-__device__ __forceinline__ typename Arith<A>::llr me_total(const DevCode& g, const MEState<A>& s,
-                                                           const typename Arith<A>::msg* X, int n) {
-  using L_ = typename Arith<A>::llr;
-  const int b0 = __ldg(g.vn_ptr + n), b1 = __ldg(g.vn_ptr + n + 1);
-  L_ acc = s.lam[n];
-  for (int k = b0; k < b1; ++k) acc = (L_)(acc + X[__ldg(g.vn_e + k)]);
-  return acc;
-}
-
-// Algorithm 4 over the set S = {n : bit n of `excl` clear}, selecting `np`
-// VNs into the bitmap s.bits (which already holds the excluded set when
-// `excl_is_bits`).  Uses s.key, s.hist, s.cnt and misc.  All threads call it.
-template <int A>
-__device__ void alg4(const DevCode& g, const MEState<A>& s, int np, int ng, uint32_t step,
-                     uint64_t frame, uint64_t seed) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int N = g.N;
+__device__ void alg4(const MEState<A>& s, int N, int np, int ng, uint32_t step, uint64_t frame, uint64_t seed) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   MEMisc* ms = s.misc;
   for (int i = tid; i < ng; i += nt) s.cnt[i] = 0;
   if (tid == 0) ms->sz = 0;
   __syncthreads();
-  int my_sz = 0;
-  for (int n = tid; n < N; n += nt) {  // line 2: G_i <- G_i u {n}, i = floor(D_n N_G)
-    if (s.bits[n >> 5] & (1u << (n & 31))) continue;
-    atomicAdd(&s.cnt[group_of(s.D[n], ng)], 1);
-    ++my_sz;
+  int my = 0;
+  for (int n = tid; n < N; n += nt) {  // line 2: |G_i|
+    if (in_bits(s.bits, n)) continue;
+    atomicAdd(&s.cnt[s.grp[n]], 1);
+    ++my;
   }
-  my_sz = __reduce_add_sync(kFull, my_sz);
-  if (lane == 0) atomicAdd(&ms->sz, my_sz);
+  my = __reduce_add_sync(kFull, my);
+  if (lane == 0 && my) atomicAdd(&ms->sz, my);
   __syncthreads();
   if (tid == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P}
     int kstar = 0, q = 0;
@@ -196,115 +140,95 @@ __device__ void alg4(const DevCode& g, const MEState<A>& s, int np, int ng, uint
       q = ms->sz;
     } else {
       for (int k = 1; k < ng; ++k) {
-        if (q + s.cnt[ng - k] <= np) {
-          q += s.cnt[ng - k];
-          kstar = k;
-        } else {
-          break;
-        }
+        if (q + s.cnt[ng - k] > np) break;
+        q += s.cnt[ng - k];
+        kstar = k;
       }
     }
+    const int need = kstar < ng ? np - q : 0;
     ms->kstar = kstar;
-    ms->need = (kstar < ng) ? np - q : 0;
+    ms->need = need;
     ms->fill_g = ng - kstar - 1;
-    ms->thr = 0;
+    ms->thr = 0xffffffffu;
+    if (need > 0) {
+      const int members = s.cnt[ng - kstar - 1];
+      const unsigned long long want = (unsigned long long)(3 * need / 2 + 48);
+      if (members > kCap / 2)
+        ms->thr = (uint32_t)min(0xffffffffull, (want << 32) / (unsigned long long)members);
+    }
+    ms->lo = 0;
+    ms->hi = 0xffffffffu;
+    ms->hi_set = 0;
+    ms->done = need == 0;
+    ms->ncand = 0;
   }
   __syncthreads();
-  const int kstar = ms->kstar, fg = ms->fill_g;
-  int need = ms->need;
-  const int top = ng - kstar;
-  if (need > 0) {
-    // keys of the fill group, then the need-th smallest key by radix select
-    for (int n = tid; n < N; n += nt) {
-      if (s.bits[n >> 5] & (1u << (n & 31))) continue;
-      if (group_of(s.D[n], ng) == fg) s.key[n] = philox_word0((uint32_t)n, step, frame, seed);
-    }
-    uint32_t prefix = 0;
-    for (int pass = 3; pass >= 0; --pass) {
-      const int shift = 8 * pass;
-      const uint32_t hmask = pass == 3 ? 0u : (0xffffffffu << (shift + 8));
-      for (int i = tid; i < 256; i += nt) s.hist[i] = 0;
-      __syncthreads();
-      for (int n = tid; n < N; n += nt) {
-        if (s.bits[n >> 5] & (1u << (n & 31))) continue;
-        if (group_of(s.D[n], ng) != fg) continue;
-        const uint32_t k = s.key[n];
-        if ((k & hmask) == (prefix & hmask)) atomicAdd(&s.hist[(k >> shift) & 255], 1);
+  const int top = ng - ms->kstar, fg = ms->fill_g, need = ms->need;
+  // lines 4-6: the `need` fill-group members with the smallest keys
+  for (int iter = 0; iter < 64; ++iter) {
+    if (ms->done) break;  // uniform: written by thread 0 before a barrier
+    const uint32_t thr = ms->thr;
+    for (int q = tid; q < (N + 3) / 4; q += nt) {
+      unsigned mem = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int n = 4 * q + i;
+        if (n < N && !in_bits(s.bits, n) && s.grp[n] == fg) mem |= 1u << i;
       }
-      __syncthreads();
-      if (warp == 0) {
-        // digit d with cum(<d) < need <= cum(<=d); lane owns digits 8 lane .. 8 lane + 7
-        int loc[8], tot = 0;
+      if (!mem) continue;
+      uint32_t w[4] = {(uint32_t)q, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
+      philox4(w, seed);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          loc[i] = s.hist[8 * lane + i];
-          tot += loc[i];
-        }
-        int incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        int before = incl - tot;
-        int found = -1, fb = 0, fc = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (found < 0 && before < need && need <= before + loc[i]) {
-            found = 8 * lane + i;
-            fb = before;
-            fc = loc[i];
-          }
-          before += loc[i];
-        }
-        const unsigned hit = __ballot_sync(kFull, found >= 0);
-        const int src = __ffs(hit) - 1;
-        const int d = __shfl_sync(kFull, found, src);
-        const int b4 = __shfl_sync(kFull, fb, src);
-        const int c4 = __shfl_sync(kFull, fc, src);
-        if (lane == 0) {
-          ms->thr = prefix | ((uint32_t)d << shift);
-          ms->need = need - b4;
-          ms->cnt_eq = c4;
+      for (int i = 0; i < 4; ++i) {
+        if (!((mem >> i) & 1u) || w[i] > thr) continue;
+        const int pos = atomicAdd(&ms->ncand, 1);
+        if (pos < kCap) s.cand[pos] = ((unsigned long long)w[i] << 32) | (unsigned)(4 * q + i);
+      }
+    }
+    __syncthreads();
+    const int nc = ms->ncand;
+    if (nc >= need && nc <= kCap) {
+      // exact rank among the candidates: (key, n) is unique
+      for (int c = tid; c < nc; c += nt) {
+        const unsigned long long kc = s.cand[c];
+        int rank = 0;
+        for (int c2 = 0; c2 < nc; ++c2) rank += s.cand[c2] < kc;
+        if (rank < need) {
+          const int n = (int)(kc & 0xffffffffull);
+          atomicOr(&s.bits[n >> 5], 1u << (n & 31));
         }
       }
-      __syncthreads();
-      prefix = ms->thr;
-      need = ms->need;
     }
+    __syncthreads();
+    if (tid == 0) {
+      if (nc >= need && nc <= kCap) {
+        ms->done = 1;
+      } else if (nc < need) {  // bisect the threshold upwards
+        ms->lo = thr;
+        ms->thr = ms->hi_set ? thr + (ms->hi - thr + 1) / 2
+                             : (thr > 0x7fffffffu ? 0xffffffffu : 2u * thr + 1u);
+      } else {  // too many: downwards
+        ms->hi = thr;
+        ms->hi_set = 1;
+        ms->thr = ms->lo + (thr - ms->lo) / 2;
+      }
+      ms->ncand = 0;
+    }
+    __syncthreads();
   }
-  const uint32_t thr = ms->thr;
-  const bool all_eq = need > 0 && ms->cnt_eq == need;
-  // selection: groups >= N_G - k* (line 3), plus fill members with key < thr
-  // (or == thr) (lines 4-6)
+  // line 3: P = Q(k*) (groups >= N_G - k*)
   for (int n = tid; n < N; n += nt) {
-    if (s.bits[n >> 5] & (1u << (n & 31))) continue;
-    const int gi = group_of(s.D[n], ng);
-    bool take = gi >= top;
-    if (!take && need > 0 && gi == fg) {
-      const uint32_t k = s.key[n];
-      take = k < thr || (k == thr && all_eq);
-    }
-    if (take) atomicOr(&s.bits[n >> 5], 1u << (n & 31));
-  }
-  __syncthreads();
-  if (need > 0 && !all_eq && tid == 0) {  // rare: equal keys at the threshold -> lowest n
-    int left = need;
-    for (int n = 0; n < N && left > 0; ++n) {
-      if (group_of(s.D[n], ng) != fg || s.key[n] != thr) continue;
-      if (s.bits[n >> 5] & (1u << (n & 31))) continue;  // excluded set (never the case for members)
-      s.bits[n >> 5] |= 1u << (n & 31);
-      --left;
-    }
+    if (s.grp[n] < top || in_bits(s.bits, n)) continue;
+    atomicOr(&s.bits[n >> 5], 1u << (n & 31));
   }
   __syncthreads();
 }
 
 // Compact the selection bitmap into s.sel (ascending) and clear it.
 template <int A>
-__device__ void compact_selection(const DevCode& g, const MEState<A>& s, int np) {
+__device__ void compact_selection(int N, const MEState<A>& s, int np) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int words = (g.N + 31) / 32;
+  const int words = (N + 31) / 32;
   if (warp == 0) {
     int base = 0;
     for (int w0 = 0; w0 < words; w0 += 32) {
@@ -334,44 +258,41 @@ __device__ void compact_selection(const DevCode& g, const MEState<A>& s, int np)
   __syncthreads();
 }
 
-template <int A, int SCHED>
+template <int A, int SCHED, class G>
 __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int64_t b = blockIdx.x;
-  const DevCode& g = a.g;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int N = g.N, E = g.E, M = g.M;
-  const int np = a.n_p, ng = a.n_g;
-  const MELayout ly = me_layout(A, M, N, E, np, g.dv_max, ng);
-  MEState<A> s;
-  s.C = (M_*)(smem_raw + ly.C);
-  s.P = (M_*)(smem_raw + ly.P);
-  s.lam = (L_*)(smem_raw + ly.lam);
-  s.L = (L_*)(smem_raw + ly.L);
-  s.Lt = (L_*)(smem_raw + ly.Lt);
-  s.D = (D_*)(smem_raw + ly.D);
-  s.par = (uint32_t*)(smem_raw + ly.par);
-  s.key = (uint32_t*)(smem_raw + ly.key);
-  s.sel = (int32_t*)(smem_raw + ly.sel);
-  s.est = (int32_t*)(smem_raw + ly.est);
-  s.best = (unsigned long long*)(smem_raw + ly.best);
-  s.cnl = (int2*)(smem_raw + ly.cnl);
-  s.hist = (int32_t*)(smem_raw + ly.hist);
-  s.cnt = (int32_t*)(smem_raw + ly.cnt);
-  s.bits = (uint32_t*)(smem_raw + ly.bits);
-  s.misc = (MEMisc*)(smem_raw + ly.misc);
   __shared__ int16_t tab_int[256];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int N = a.g.N, E = a.g.E, M = a.g.M;
+  const int np = a.n_p, ng = a.n_g;
+  const MELayout ly = me_layout(A, M, N, E, np, a.g.dv_max, ng);
+  unsigned char* base = smem_raw + a.graph_smem;
+  MEState<A> s;
+  s.C = (M_*)(base + ly.C);
+  s.P = (M_*)(base + ly.P);
+  s.lam = (L_*)(base + ly.lam);
+  s.L = (L_*)(base + ly.L);
+  s.D = (D_*)(base + ly.D);
+  s.grp = (uint8_t*)(base + ly.grp);
+  s.par = (uint32_t*)(base + ly.par);
+  s.sel = (int32_t*)(base + ly.sel);
+  s.est = (int32_t*)(base + ly.est);
+  s.best = (unsigned long long*)(base + ly.best);
+  s.cnl = (int2*)(base + ly.cnl);
+  s.cand = (unsigned long long*)(base + ly.cand);
+  s.cnt = (int32_t*)(base + ly.cnt);
+  s.bits = (uint32_t*)(base + ly.bits);
+  s.misc = (MEMisc*)(base + ly.misc);
   s.tab = tab_int;
   MEMisc* ms = s.misc;
   const float clip = a.llr_clip;
   const uint64_t frame = a.frame_offset + (uint64_t)b;
-  int W = 1;
-  while (W < g.dc_max) W <<= 1;
-  const int tpw = 32 / W;  // teams per warp
-  const int team = lane / W, r = lane % W;
+  const int W = a.team_w, tpw = 32 / W, team = lane / W, r = lane % W;
 
   if (A == kINT6)
     for (int i = tid; i < 256; i += nt) tab_int[i] = a.ci_table[i];
@@ -409,22 +330,23 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
   // ---- Alg. 5/6 lines 1-3: every L~^C, R, L~, D; syndrome of bsgn(lambda)
   for (int t0 = warp * tpw; t0 < M; t0 += nw * tpw) {
     const int m = t0 + team;
-    team_c2v<A>(g, s, m < M ? m : -1, r, W, clip);
-  }
-  for (int m = tid; m < M; m += nt) {
-    const int c0 = __ldg(g.cn_ptr + m), c1 = __ldg(g.cn_ptr + m + 1);
-    unsigned p = 0;
-    for (int e = c0; e < c1; ++e) p ^= (s.L[__ldg(g.e_vn + e)] < (L_)0);
-    if (p) {
+    int e, j;
+    M_ out;
+    const int dc = team_c2v<A, G>(g, s.C, s.L, m < M ? m : -1, r, W, clip, e, j, out);
+    if (r < dc) s.P[e] = out;
+    const unsigned neg = __ballot_sync(kFull, r < dc && s.L[j] < (L_)0);
+    const unsigned tmask = (W == 32 ? kFull : ((1u << W) - 1u)) << (team * W);
+    if (r == 0 && m < M && (__popc(neg & tmask) & 1)) {
       atomicOr(&s.par[m >> 5], 1u << (m & 31));
       atomicAdd(&ms->unsat, 1);
     }
   }
   __syncthreads();
   for (int n = tid; n < N; n += nt) {
-    const L_ lt = me_total<A>(g, s, s.P, n);
-    s.Lt[n] = lt;
-    s.D[n] = ci_me(s, s.L[n], lt);
+    const L_ lt = vn_total<A, G>(g, s.lam, s.P, n);
+    const D_ d = ci_me(s, s.L[n], lt);
+    s.D[n] = d;
+    s.grp[n] = (uint8_t)group_of(d, ng);
   }
   __syncthreads();
 
@@ -432,8 +354,8 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
   uint32_t step = 0;
   bool stop = a.check_interval > 0 && ms->unsat == 0;
   if (!stop && a.max_updates > 0) {  // Alg. 5 line 4 / Alg. 6 line 4
-    alg4<A>(g, s, np, ng, step, frame, a.seed);
-    compact_selection<A>(g, s, np);
+    alg4<A>(s, N, np, ng, step, frame, a.seed);
+    compact_selection<A>(N, s, np);
   }
   while (!stop && count < a.max_updates) {
     int nsel = ms->nsel;
@@ -442,11 +364,12 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
     // -- m*_p = argmax_i R_{i->p}, i in M(p), on the pre-step state
     for (int k = tid; k < nsel; k += nt) {
       const int p = s.sel[k];
-      const int v0 = __ldg(g.vn_ptr + p), v1 = __ldg(g.vn_ptr + p + 1);
+      const typename G::V v = g.vn(p);
       uint32_t bk = 0, bi = 0xffffffffu;
-      for (int q = v0; q < v1; ++q) {
-        const int e = __ldg(g.vn_e + q);
-        am_update(bk, bi, rkey_me(s.P[e], s.C[e]), (uint32_t)e);
+      for (int q = 0; q < v.d; ++q) {
+        int e, m;
+        g.vedge(v, q, e, m);
+        am_update(bk, bi, rkey(s.P[e], s.C[e]), (uint32_t)e);
       }
       s.est[k] = (int)bi;
       s.best[k] = 0ull;
@@ -455,21 +378,22 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
     __syncthreads();
     // -- commits, L_p, syndrome, trace, affected checks i in M(p)\m*_p
     for (int k = tid; k < nsel; k += nt) {
-      const int p = s.sel[k], es = s.est[k], ms_ = __ldg(g.e_cn + es);
+      const int p = s.sel[k], es = s.est[k];
       s.C[es] = s.P[es];
       const L_ lold = s.L[p];
-      const L_ lnew = me_total<A>(g, s, s.C, p);
+      const L_ lnew = vn_total<A, G>(g, s.lam, s.C, p);
       s.L[p] = lnew;
       const bool flip = (lold < (L_)0) != (lnew < (L_)0);
-      const int v0 = __ldg(g.vn_ptr + p), v1 = __ldg(g.vn_ptr + p + 1);
-      for (int q = v0; q < v1; ++q) {
-        const int m = __ldg(g.e_cn + __ldg(g.vn_e + q));
-        if (flip) {
+      const typename G::V v = g.vn(p);
+      for (int q = 0; q < v.d; ++q) {
+        int e, m;
+        g.vedge(v, q, e, m);
+        if (flip) {  // tentative decision of p flipped: parity of every check of p
           const uint32_t bit = 1u << (m & 31);
           const uint32_t old = atomicXor(&s.par[m >> 5], bit);
           atomicAdd(&ms->unsat, (old & bit) ? -1 : 1);
         }
-        if (m != ms_) {
+        if (e != es) {
           const int pos = atomicAdd(&ms->ncn, 1);
           s.cnl[pos] = make_int2(m, k);
         }
@@ -481,7 +405,10 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
     // -- precomputed C2V of every affected check
     for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
       const int t = t0 + team;
-      team_c2v<A>(g, s, t < ncn ? s.cnl[t].x : -1, r, W, clip);
+      int e, j;
+      M_ out;
+      const int dc = team_c2v<A, G>(g, s.C, s.L, t < ncn ? s.cnl[t].x : -1, r, W, clip, e, j, out);
+      if (r < dc) s.P[e] = out;
     }
     __syncthreads();
     // -- L~_j, D_j next to affected checks (and of every p); LMD candidates
@@ -489,13 +416,13 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
       const int t = t0 + team;
       if (t >= ncn) continue;
       const int2 ck = s.cnl[t];
-      const int c0 = __ldg(g.cn_ptr + ck.x), dc = __ldg(g.cn_ptr + ck.x + 1) - c0;
-      if (r >= dc) continue;
-      const int j = __ldg(g.e_vn + c0 + r);
-      const L_ lt = me_total<A>(g, s, s.P, j);
+      const typename G::C cc = g.cn(ck.x);
+      if (r >= cc.d) continue;
+      const int j = g.cvn(cc, r);
+      const L_ lt = vn_total<A, G>(g, s.lam, s.P, j);
       const D_ d = ci_me(s, s.L[j], lt);
-      s.Lt[j] = lt;
       s.D[j] = d;
+      s.grp[j] = (uint8_t)group_of(d, ng);
       if (SCHED == kMELMD && j != s.sel[ck.y]) {
         const unsigned long long key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
         atomicMax(&s.best[ck.y], key);
@@ -503,9 +430,10 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
     }
     for (int k = tid; k < nsel; k += nt) {
       const int p = s.sel[k];
-      const L_ lt = me_total<A>(g, s, s.P, p);
-      s.Lt[p] = lt;
-      s.D[p] = ci_me(s, s.L[p], lt);
+      const L_ lt = vn_total<A, G>(g, s.lam, s.P, p);
+      const D_ d = ci_me(s, s.L[p], lt);
+      s.D[p] = d;
+      s.grp[p] = (uint8_t)group_of(d, ng);
     }
     __syncthreads();
     count += nsel;
@@ -515,19 +443,18 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
       break;
     if (count >= a.max_updates) break;
     if (SCHED == kMECIRBP) {
-      alg4<A>(g, s, np, ng, step, frame, a.seed);  // Alg. 5 line 4
-      compact_selection<A>(g, s, np);
+      alg4<A>(s, N, np, ng, step, frame, a.seed);  // Alg. 5 line 4
+      compact_selection<A>(N, s, np);
       continue;
     }
-    // -- Alg. 6 lines 6-10: P' = {argmax_{j in U(m*_p, p)} D_j}; degree-1 rule
+    // -- Alg. 6 lines 6-10: P' = {argmax_{j in U(m*_p, p)} D_j}; degree-1 rule (Sec. 5.A)
     for (int k = tid; k < nsel; k += nt) {
       const int p = s.sel[k];
-      if (__ldg(g.vn_ptr + p + 1) - __ldg(g.vn_ptr + p) == 1) {
-        const int mm = __ldg(g.e_cn + s.est[k]);
-        const int c0 = __ldg(g.cn_ptr + mm), c1 = __ldg(g.cn_ptr + mm + 1);
+      if (g.vn(p).d == 1) {
+        const typename G::C cc = g.cn(g.ecn(s.est[k]));
         unsigned long long bk = 0ull;
-        for (int e = c0; e < c1; ++e) {
-          const int j = __ldg(g.e_vn + e);
+        for (int q = 0; q < cc.d; ++q) {
+          const int j = g.cvn(cc, q);
           if (j == p) continue;
           const unsigned long long key = ((unsigned long long)mkey(s.D[j]) << 32) | (0xffffffffu - (uint32_t)j);
           bk = key > bk ? key : bk;
@@ -550,8 +477,8 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
     if (lane == 0 && mine) atomicAdd(&ms->npp, mine);
     __syncthreads();
     const int npp = ms->npp;
-    if (npp < np) alg4<A>(g, s, np - npp, ng, step, frame, a.seed);  // lines 11-13
-    compact_selection<A>(g, s, np);
+    if (npp < np) alg4<A>(s, N, np - npp, ng, step, frame, a.seed);  // lines 11-13
+    compact_selection<A>(N, s, np);
   }
 
   for (int n = tid; n < N; n += nt) {
@@ -564,19 +491,25 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
   }
 }
 
-template <int A, int S>
+template <int A, int S, class G>
 cudaError_t launch_me_one(const DecodeArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.smem_per_frame;
-  auto k = me_decode_kernel<A, S>;
+  const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame;
+  auto k = me_decode_kernel<A, S, G>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k<<<(unsigned)a.batch, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+template <int A, class G>
+cudaError_t launch_me_sched(const DecodeArgs& a, int sched, cudaStream_t s) {
+  if (sched == kMECIRBP) return launch_me_one<A, kMECIRBP, G>(a, s);
+  return launch_me_one<A, kMELMD, G>(a, s);
+}
+
 }  // namespace
 
-size_t me_smem_per_frame(int arith, int sched, const DevCode& g, int n_p, int n_g) {
+size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g) {
   (void)sched;
   if (g.dc_max > 32) return 0;
   return (size_t)me_layout(arith, g.M, g.N, g.E, n_p, g.dv_max, n_g).total;
@@ -584,12 +517,9 @@ size_t me_smem_per_frame(int arith, int sched, const DevCode& g, int n_p, int n_
 
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s) {
   if (a.batch == 0) return cudaSuccess;
-  if (arith == kFP32) {
-    if (sched == kMECIRBP) return launch_me_one<kFP32, kMECIRBP>(a, s);
-    return launch_me_one<kFP32, kMELMD>(a, s);
-  }
-  if (sched == kMECIRBP) return launch_me_one<kINT6, kMECIRBP>(a, s);
-  return launch_me_one<kINT6, kMELMD>(a, s);
+  if (arith == kFP32)
+    return a.g.is_qc ? launch_me_sched<kFP32, QCGraph>(a, sched, s) : launch_me_sched<kFP32, TabGraph>(a, sched, s);
+  return a.g.is_qc ? launch_me_sched<kINT6, QCGraph>(a, sched, s) : launch_me_sched<kINT6, TabGraph>(a, sched, s);
 }
 
 }  // namespace ldpc

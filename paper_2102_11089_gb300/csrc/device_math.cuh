@@ -1,9 +1,10 @@
 // device_math.cuh -- message arithmetic of the decoders (FP32 sum-product and
-// 6-bit integer min-sum) and warp-level argmax helpers.
+// 6-bit integer min-sum), check-team combination and warp argmax helpers.
 #pragma once
 
 #include <cstdint>
 
+#include "graph.cuh"
 #include "internal.h"
 
 namespace ldpc {
@@ -22,39 +23,61 @@ template <> struct Arith<kINT6> {
   using dval = uint16_t;
 };
 
-// phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)) for x >= 0; phi is its own
-// inverse and turns the product of tanh terms of eq. (2) into a sum:
-// 2 atanh(prod tanh(|V_k|/2)) = phi(sum phi(|V_k|)).  phi(0) = +inf, phi(inf) = 0.
-__device__ __forceinline__ float phi_f(float x) { return log1pf(2.0f / expm1f(x)); }
+// 1 - e^-x for 0 <= x < 1/4 by its Taylor polynomial to x^6 (relative error < 6e-8)
+__device__ __forceinline__ float one_minus_exp_small(float x) {
+  return x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x * (1.0f / 720.0f))))));
+}
 
-// The scratch value of one V2C input of a check: its phi with the sign of V
-// in the sign bit (V < 0 gives a set sign bit, also when phi is 0).
+// phi(x) = -ln tanh(x/2) = 2 atanh(e^-x) for x >= 0; phi(0) = +inf, phi(inf) = 0.
+// phi is its own inverse and turns eq. (2) into sums:
+// 2 atanh(prod tanh(|V_k|/2)) = phi(sum phi(|V_k|)).
+// With t = e^-x: for t <= 1/4 the odd series 2t(1 + t^2/3 + ... + t^10/11)
+// (truncation < 5e-9 relative); above, ln((1+t)/(1-t)) with 1 - t from the Taylor
+// polynomial when x < 1/4 (no cancellation) and MUFU lg2.  Relative error ~1e-6
+// (the exponential itself is the accurate expf: MUFU ex2 alone loses |x| 1e-7).
+__device__ __forceinline__ float phi_f(float x) {
+  const float t = expf(-x);
+  if (t <= 0.25f) {
+    const float t2 = t * t;
+    float p = 1.0f / 11.0f;
+    p = fmaf(p, t2, 1.0f / 9.0f);
+    p = fmaf(p, t2, 1.0f / 7.0f);
+    p = fmaf(p, t2, 0.2f);
+    p = fmaf(p, t2, 1.0f / 3.0f);
+    p = fmaf(p, t2, 1.0f);
+    return 2.0f * t * p;
+  }
+  const float omt = x < 0.25f ? one_minus_exp_small(x) : 1.0f - t;
+  return __logf(__fdividef(1.0f + t, omt));
+}
+
+// The encoded V2C input of a check: phi(|V| clipped) with the sign of V in the
+// sign bit (V < 0 gives a set sign bit, also when phi is 0).
 __device__ __forceinline__ float encode_fp(float v, float clip) {
-  const float a = fminf(fabsf(v), clip);
-  const float p = phi_f(a);
+  const float p = phi_f(fminf(fabsf(v), clip));
   return v < 0.0f ? -p : p;
 }
 
-// Combine every other entry of a check (exclude-one): sign product and phi of
-// the sum of phis, clamped to +-clip.  Matches eq. (2) with the V2C clip.
+// sign product and phi of the sum of phis, clamped to +-clip (eq. 2)
 __device__ __forceinline__ float combine_fp(float sum_phi, unsigned neg, float clip) {
-  float m = fminf(phi_f(sum_phi), clip);
+  const float m = fminf(phi_f(sum_phi), clip);
   return neg ? -m : m;
 }
 
 __device__ __forceinline__ int8_t encode_int(int v) { return (int8_t)max(-31, min(31, v)); }
 
-// |p0(a) - p0(b)| of eq. (8) with p0(L) = e^L/(1+e^L), written to avoid the
-// cancellation of 1 - 1: for equal signs it is |e^-y - e^-x| / ((1+e^-x)(1+e^-y))
-// with x = |a|, y = |b|; for opposite signs (tanh(|a|/2) + tanh(|b|/2)) / 2.
+// |p0(a) - p0(b)| of eq. (8), p0(L) = e^L/(1+e^L), without the cancellation of
+// 1 - 1: with x = |a|, y = |b|, ex = e^-x, ey = e^-y,
+//   equal signs    : e^-min(x,y) (1 - e^-|x-y|) / ((1+ex)(1+ey))
+//   opposite signs : ((1-ex)/(1+ex) + (1-ey)/(1+ey)) / 2  (= (tanh(x/2)+tanh(y/2))/2)
 __device__ __forceinline__ float ci_fp(float a, float b) {
-  const bool sa = a >= 0.0f, sb = b >= 0.0f;
   const float x = fabsf(a), y = fabsf(b);
-  if (sa != sb) return 0.5f * (tanhf(0.5f * x) + tanhf(0.5f * y));
-  const float lo = fminf(x, y), d = fabsf(x - y);
-  const float num = -expf(-lo) * expm1f(-d);
-  const float den = (1.0f + expf(-x)) * (1.0f + expf(-y));
-  return num / den;
+  const float ex = expf(-x), ey = expf(-y);
+  if ((a >= 0.0f) != (b >= 0.0f))
+    return 0.5f * (__fdividef(1.0f - ex, 1.0f + ex) + __fdividef(1.0f - ey, 1.0f + ey));
+  const float d = fabsf(x - y);
+  const float omd = d < 0.25f ? one_minus_exp_small(d) : 1.0f - expf(-d);
+  return __fdividef(fmaxf(ex, ey) * omd, (1.0f + ex) * (1.0f + ey));
 }
 
 // Integer CI: |T[c(a)] - T[c(b)]| with c = clamp to [-127, 127].
@@ -69,9 +92,16 @@ __device__ __forceinline__ uint32_t mkey(float v) { return __float_as_uint(v); }
 __device__ __forceinline__ uint32_t mkey(int v) { return (uint32_t)v; }
 __device__ __forceinline__ uint32_t mkey(uint16_t v) { return (uint32_t)v; }
 
+// residual |L~^C - L^C| (eq. 4) as a key
+__device__ __forceinline__ uint32_t rkey(float p, float c) { return mkey(fabsf(p - c)); }
+__device__ __forceinline__ uint32_t rkey(int8_t p, int8_t c) { return (uint32_t)abs((int)p - (int)c); }
+
 // Running argmax of (key, idx): larger key wins, equal keys go to the lower idx.
 __device__ __forceinline__ void am_update(uint32_t& bk, uint32_t& bi, uint32_t k, uint32_t i) {
-  if (k > bk || (k == bk && i < bi)) { bk = k; bi = i; }
+  if (k > bk || (k == bk && i < bi)) {
+    bk = k;
+    bi = i;
+  }
 }
 
 // Warp-wide argmax; lanes without a candidate pass (0, 0xffffffff).  Returns the
@@ -85,6 +115,68 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// Check team: W lanes (power of two) handle check m (m < 0: idle).  Lane r < dc
+// owns edge e = base + r towards variable j; V2C = L_j - C[e] (eq. 1); `out`
+// receives the exclude-one combination over the other edges (eq. 2 / min-sum).
+// All lanes of the warp must call it (width-W shuffles).  Returns dc.
+template <int A, class G>
+__device__ __forceinline__ int team_c2v(const G& g, const typename Arith<A>::msg* C,
+                                        const typename Arith<A>::llr* L, int m, int r, int W,
+                                        float clip, int& e, int& j, typename Arith<A>::msg& out) {
+  int dc = 0;
+  e = 0;
+  j = 0;
+  if (m >= 0) {
+    const typename G::C cc = g.cn(m);
+    dc = cc.d;
+    if (r < dc) {
+      e = cc.b + r;
+      j = g.cvn(cc, r);
+    }
+  }
+  if (A == kFP32) {
+    const float enc = r < dc ? encode_fp((float)L[j] - (float)C[e], clip) : 0.0f;
+    float sum = 0.0f;
+    unsigned neg = 0;
+    for (int k = 0; k < W; ++k) {
+      const float v = __shfl_sync(kFull, enc, k, W);
+      if (k != r && k < dc) {
+        sum += fabsf(v);
+        neg ^= __float_as_uint(v) >> 31;
+      }
+    }
+    out = (typename Arith<A>::msg)combine_fp(sum, neg, clip);
+  } else {
+    const int enc = r < dc ? (int)encode_int((int)L[j] - (int)C[e]) : 0;
+    int mag = 31;
+    unsigned neg = 0;
+    for (int k = 0; k < W; ++k) {
+      const int v = __shfl_sync(kFull, enc, k, W);
+      if (k != r && k < dc) {
+        neg ^= (v < 0);
+        mag = min(mag, abs(v));
+      }
+    }
+    out = (typename Arith<A>::msg)(neg ? -mag : mag);
+  }
+  return dc;
+}
+
+// lam[n] + sum_{m in M(n)} X[e]  (eq. 3 with X = L^C, Sec. 2.B with X = L~^C)
+template <int A, class G, typename X>
+__device__ __forceinline__ typename Arith<A>::llr vn_total(const G& g, const typename Arith<A>::llr* lam,
+                                                           const X* arr, int n) {
+  using L_ = typename Arith<A>::llr;
+  const typename G::V v = g.vn(n);
+  L_ acc = lam[n];
+  for (int k = 0; k < v.d; ++k) {
+    int e, m;
+    g.vedge(v, k, e, m);
+    acc = (L_)(acc + arr[e]);
+  }
+  return acc;
 }
 
 }  // namespace ldpc

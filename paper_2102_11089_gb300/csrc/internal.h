@@ -18,20 +18,26 @@ constexpr int kLMD = 3;
 constexpr int kMECIRBP = 4;
 constexpr int kMELMD = 5;
 
-// Tanner graph in device memory (canonical CSR edge order: by check, then variable).
-struct DevCode {
+// Device view of a code (canonical CSR edge order: by check, then variable).
+// `tab` = cn_ptr[M+1] | e_vn[E] | e_cn[E] | vn_ptr[N+1] | vn_e[E] (int32), always
+// present.  For codes lifted from a protograph `qc` holds
+// rowbase[R+1] | rowfirst[R+1] | colfirst[C+1] | rowblk[nnz] | colblk[nnz].
+struct GraphDesc {
   int32_t M, N, E;
   int32_t dv_max, dc_max, maxr;  // maxr = max_n sum_{m in M(n)} |N(m)|
-  const int32_t* cn_ptr;         // M+1: edges of check m are [cn_ptr[m], cn_ptr[m+1])
-  const int32_t* e_vn;           // E  : variable node of edge e
-  const int32_t* e_cn;           // E  : check node of edge e
-  const int32_t* vn_ptr;         // N+1
-  const int32_t* vn_e;           // E  : edges of variable n, ascending check index
+  const int32_t* tab;
+  int32_t tab_words;
+  int32_t tab_in_smem;  // stage the tables into shared memory
+  const int32_t* qc;
+  int32_t qc_words;
+  int32_t qc_R, qc_C, qc_Z, qc_nnz;
+  uint32_t qc_zmul, qc_zshift;
+  int32_t is_qc;
 };
 
 // Everything a decode kernel needs, passed by value.
 struct DecodeArgs {
-  DevCode g;
+  GraphDesc g;
   const void* llr;  // [batch][N] float (FP32) or int8 (INT6)
   int64_t batch;
   uint8_t* hard;
@@ -47,22 +53,27 @@ struct DecodeArgs {
   int32_t n_p, n_g;
   uint64_t seed;
   uint64_t frame_offset;
-  uint32_t* status;       // device status word (bit 0: bad input seen)
-  void* gstate;           // global-memory frame state (LDPC_FORM_GLOBAL), else null
-  int64_t gstate_stride;  // bytes per frame of gstate
+  uint32_t* status;  // device status word (bit 0: bad input seen)
   int32_t frames_per_cta;
   int32_t smem_per_frame;
+  int32_t graph_smem;    // bytes of staged graph tables at the start of shared memory
+  int32_t team_w;        // lanes per check team: power of two >= max check degree
   int16_t ci_table[256];  // INT6: round(32767 tanh(q * q_step / 2)), q = -127..127
 };
 
 inline __host__ __device__ int align16(int x) { return (x + 15) & ~15; }
 
+inline __host__ __device__ int graph_smem_bytes(const GraphDesc& d) {
+  if (d.is_qc) return align16(d.qc_words * 4);
+  return d.tab_in_smem ? align16(d.tab_words * 4) : 0;
+}
+
 // Per-frame state layout of the single-edge (warp per frame) decoder.
 struct SELayout {
-  int C, P, lam, L, Lt, D, Rmax, Ridx, par, fe, fs, fj, scr, tab, total;
+  int C, P, lam, L, Lt, D, Rmax, Ridx, par, tab, total;
 };
 
-inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, int maxr, bool need_r) {
+inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bool need_r) {
   const int msg = arith == kINT6 ? 1 : 4;
   const int llr = arith == kINT6 ? 2 : 4;
   const int dv = arith == kINT6 ? 2 : 4;
@@ -77,10 +88,6 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, in
   l.Rmax = o; o = align16(o + (need_r ? M * msg : 0));
   l.Ridx = o; o = align16(o + (need_r ? M * 4 : 0));
   l.par = o; o = align16(o + ((M + 31) / 32) * 4);
-  l.fe = o; o = align16(o + maxr * 4);
-  l.fs = o; o = align16(o + maxr * 4);
-  l.fj = o; o = align16(o + maxr * 4);
-  l.scr = o; o = align16(o + maxr * 4);
   l.tab = o; o = align16(o + (arith == kINT6 ? 256 * 2 : 0));
   l.total = o;
   return l;
@@ -88,7 +95,7 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, in
 
 // Per-frame state layout of the flooding (CTA per frame) decoder.
 struct FloodLayout {
-  int C, S, lam, L, tab, total;
+  int C, lam, L, total;
 };
 
 inline __host__ __device__ FloodLayout flood_layout(int arith, int N, int E) {
@@ -97,10 +104,8 @@ inline __host__ __device__ FloodLayout flood_layout(int arith, int N, int E) {
   FloodLayout l;
   int o = 0;
   l.C = o; o = align16(o + E * msg);
-  l.S = o; o = align16(o + E * 4);
   l.lam = o; o = align16(o + N * llr);
   l.L = o; o = align16(o + N * llr);
-  l.tab = o; o = align16(o + 0);
   l.total = o;
   return l;
 }
@@ -109,12 +114,12 @@ inline __host__ __device__ FloodLayout flood_layout(int arith, int N, int E) {
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
 cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s);
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
-cudaError_t launch_channel(const DevCode& g, const uint8_t* punct, float rate, const float* ebn0,
-                           int64_t batch, uint64_t seed, uint64_t frame_offset, float* llr,
-                           int8_t* qllr, float q_step, cudaStream_t s);
+cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float* ebn0, int64_t batch,
+                           uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
+                           cudaStream_t s);
 
-size_t se_smem_per_frame(int arith, int sched, const DevCode& g);
-size_t flood_smem_per_frame(int arith, const DevCode& g);
-size_t me_smem_per_frame(int arith, int sched, const DevCode& g, int n_p, int n_g);
+size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g);
+size_t flood_smem_per_frame(int arith, const GraphDesc& g);
+size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g);
 
 }  // namespace ldpc

@@ -4,8 +4,8 @@ the same seeded inputs and compare by the acceptance rules.
 Acceptance (6-bit min-sum): decisions, update counts, final LLRs and the full
 edge-selection trace bit-exact.  FP32 sum-product: per-value |d| <= 1e-4
 max(1, |m|) against FP64; dynamic-schedule traces identical up to the first
-step whose oracle top-2 metric gap is below 1e-5; FER inside the oracle's 95%
-Clopper-Pearson interval on the same frames.
+step whose oracle top-2 metric gap (relative to max(1, |metric|)) is below
+1e-5; FER inside the oracle's 95% Clopper-Pearson interval on the same frames.
 """
 from __future__ import annotations
 
