@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--arith", default="fp32")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--decode-only", action="store_true",
+                    help="generate one batch with the channel kernel and time --reps decode launches "
+                         "(the command the ncu captures under profiles/ use)")
+    ap.add_argument("--reps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -434,8 +438,34 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
     return res
 
 
+def run_decode_only(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2102_11089_gb300 as L
+    design, Z = workload(args)
+    code = L.Code.from_protograph(design.shifts(Z), Z, design.info_cols * Z, design.punct_cols)
+    eb = torch.full((args.batch,), args.ebn0, dtype=torch.float32, device="cuda")
+    llr, q = L.awgn_llr(code, eb, seed=2021, quantize=args.arith == "int6")
+    x = q if args.arith == "int6" else llr
+    p = L.make_params(args.schedule, args.arith, gamma=0.1, n_p=args.n_p, n_g=args.n_g,
+                      max_updates=int(args.budget_iters * code.E), check_interval=1, seed=1234)
+    for _ in range(args.reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = L.decode(code, x, p)
+        b.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"schedule": args.schedule, "arith": args.arith, "batch": args.batch,
+                          "ms": a.elapsed_time(b), "mean_updates": out["updates"].float().mean().item(),
+                          "fer": fer_of(out)}))
+
+
 def main():
     args = parse()
+    if args.decode_only:
+        run_decode_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

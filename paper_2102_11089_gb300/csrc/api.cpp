@@ -495,36 +495,62 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   const int optin = max_optin_smem();
   const cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e;
-  if (p->form == LDPC_FORM_GLOBAL)
-    return fail(LDPC_ERR_UNSUPPORTED, "global-memory form not available for this schedule");
   if (g->dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
   const int gsm = a.graph_smem;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  // Form: frame state in shared memory when it fits (LDPC_FORM_AUTO / SMEM), else
+  // (or on request) in global-memory slots that persistent CTAs/warps reuse.
+  size_t per = 0, cta_fixed = 0;
   if (p->schedule == LDPC_FLOODING) {
-    const size_t per = ldpc::flood_smem_per_frame(arith, *g);
-    if ((int)per + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "code too large for the flooding kernel");
-    a.smem_per_frame = (int32_t)per;
-    a.frames_per_cta = 1;
-    e = ldpc::launch_flood(a, arith, s);
+    per = ldpc::flood_smem_per_frame(arith, *g);
   } else if (p->schedule <= LDPC_LMD_CIRBP) {
     if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
-    const size_t per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
-    if ((int)per + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+    per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
+  } else {
+    if (p->n_g > 255) return fail(LDPC_ERR_UNSUPPORTED, "n_g > 255 for the multi-edge kernel");
+    per = ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g);
+    cta_fixed = ldpc::me_smem_per_cta(*g, p->n_p, p->n_g) + 1024;  // + static table headroom
+  }
+  const bool fits = (int64_t)per + (int64_t)cta_fixed + gsm <= optin;
+  if (p->form == LDPC_FORM_SMEM && !fits) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+  if ((int64_t)cta_fixed + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "working set exceeds shared memory");
+  const bool global_form = p->form == LDPC_FORM_GLOBAL || !fits;
+  void* scratch = nullptr;
+  a.smem_per_frame = (int32_t)per;
+  if (global_form) {
+    const int64_t stride = ((int64_t)per + 255) & ~(int64_t)255;
+    int fpc = 1;
+    int64_t ctas;
+    if (p->schedule >= LDPC_RBP && p->schedule <= LDPC_LMD_CIRBP) {
+      fpc = (int)std::min<int64_t>(8, batch);
+      ctas = std::min<int64_t>((batch + fpc - 1) / fpc, (int64_t)sms * 4);
+    } else {
+      ctas = std::min<int64_t>(batch, (int64_t)sms * 2);
+    }
+    const size_t bytes = (size_t)(ctas * fpc) * (size_t)stride;
+    e = cudaMallocAsync(&scratch, bytes, s);
+    if (e != cudaSuccess) return fail(LDPC_ERR_NOMEM, std::string("cudaMallocAsync(state): ") + cudaGetErrorString(e));
+    a.gstate = scratch;
+    a.gstate_stride = stride;
+    a.gstate_ctas = (int32_t)ctas;
+    a.frames_per_cta = fpc;
+  } else if (p->schedule >= LDPC_RBP && p->schedule <= LDPC_LMD_CIRBP) {
     // frames per CTA: fill about half the opt-in shared memory so two CTAs share an SM
     int fpc = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t)std::max(0, optin / 2 - gsm) / per));
     while (fpc > 1 && (int)(fpc * per) + gsm > optin) --fpc;
     if ((int64_t)fpc > batch) fpc = (int)batch;
-    a.smem_per_frame = (int32_t)per;
     a.frames_per_cta = fpc;
-    e = ldpc::launch_se(a, arith, p->schedule, s);
   } else {
-    const size_t per = ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g);
-    // 1 KB of headroom for the kernel's static shared table
-    if (per == 0 || (int)per + gsm + 1024 > optin)
-      return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
-    if (p->n_g > 255) return fail(LDPC_ERR_UNSUPPORTED, "n_g > 255 for the multi-edge kernel");
-    a.smem_per_frame = (int32_t)per;
     a.frames_per_cta = 1;
-    e = ldpc::launch_me(a, arith, p->schedule, s);
+  }
+  if (p->schedule == LDPC_FLOODING) e = ldpc::launch_flood(a, arith, s);
+  else if (p->schedule <= LDPC_LMD_CIRBP) e = ldpc::launch_se(a, arith, p->schedule, s);
+  else e = ldpc::launch_me(a, arith, p->schedule, s);
+  if (scratch) {
+    const cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return LDPC_OK;

@@ -11,16 +11,13 @@ namespace ldpc {
 
 namespace {
 
+// Decode frame b with its state at `base` (shared or global memory).
 template <int A, class G>
-__global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
+__device__ __forceinline__ void flood_frame(const DecodeArgs& a, const G& g, int64_t b, unsigned char* base) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
-  const int64_t b = blockIdx.x;
   const int N = a.g.N, E = a.g.E, M = a.g.M;
   const FloodLayout ly = flood_layout(A, N, E);
-  unsigned char* base = smem_raw + a.graph_smem;
   M_* C = (M_*)(base + ly.C);
   L_* lam = (L_*)(base + ly.lam);
   L_* L = (L_*)(base + ly.L);
@@ -95,16 +92,41 @@ __global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
     if (a.updates) a.updates[b] = count;
     if (a.converged) a.converged[b] = (uint8_t)conv;
   }
+  __syncthreads();
 }
 
 template <int A, class G>
+__global__ void __launch_bounds__(512) flood_decode_kernel(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  flood_frame<A, G>(a, g, blockIdx.x, smem_raw + a.graph_smem);
+}
+
+// Global-memory form: CTA c owns state slot c and decodes frames c + k gridDim.x.
+template <int A, class G>
+__global__ void __launch_bounds__(512) flood_decode_kernel_gs(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  unsigned char* base = (unsigned char*)a.gstate + (int64_t)blockIdx.x * a.gstate_stride;
+  for (int64_t b = blockIdx.x; b < a.batch; b += gridDim.x) flood_frame<A, G>(a, g, b, base);
+}
+
+int flood_threads(const DecodeArgs& a) { return a.g.E >= 4096 ? 512 : (a.g.E >= 1024 ? 256 : 128); }
+
+template <int A, class G>
 cudaError_t launch_g(const DecodeArgs& a, cudaStream_t s) {
+  if (a.gstate) {
+    auto k = flood_decode_kernel_gs<A, G>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.graph_smem);
+    if (err != cudaSuccess) return err;
+    k<<<(unsigned)a.gstate_ctas, flood_threads(a), a.graph_smem, s>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame;
-  const int threads = a.g.E >= 4096 ? 512 : (a.g.E >= 1024 ? 256 : 128);
   auto k = flood_decode_kernel<A, G>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k<<<(unsigned)a.batch, threads, smem, s>>>(a);
+  k<<<(unsigned)a.batch, flood_threads(a), smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -26,15 +26,20 @@ namespace {
 
 constexpr int kCap = 1024;  // candidate list of the random fill
 
-struct MELayout {
-  int C, P, lam, L, D, grp, par, sel, est, best, cnl, cand, cnt, bits, misc, total;
+// Big per-frame arrays (shared memory, or a global-memory slot for large codes)
+struct MEBig {
+  int C, P, lam, L, D, grp, par, total;
+};
+// Per-CTA working set of one step (always shared memory)
+struct MESmall {
+  int sel, est, best, cnl, cand, cnt, bits, misc, total;
 };
 
-__host__ __device__ inline MELayout me_layout(int arith, int M, int N, int E, int n_p, int dvm, int n_g) {
+__host__ __device__ inline MEBig me_big(int arith, int M, int N, int E) {
   const int msg = arith == kINT6 ? 1 : 4;
   const int llr = arith == kINT6 ? 2 : 4;
   const int dv = arith == kINT6 ? 2 : 4;
-  MELayout l;
+  MEBig l;
   int o = 0;
   l.C = o; o = align16(o + E * msg);
   l.P = o; o = align16(o + E * msg);
@@ -43,6 +48,13 @@ __host__ __device__ inline MELayout me_layout(int arith, int M, int N, int E, in
   l.D = o; o = align16(o + N * dv);
   l.grp = o; o = align16(o + N);
   l.par = o; o = align16(o + ((M + 31) / 32) * 4);
+  l.total = o;
+  return l;
+}
+
+__host__ __device__ inline MESmall me_small(int N, int n_p, int dvm, int n_g) {
+  MESmall l;
+  int o = 0;
   l.sel = o; o = align16(o + n_p * 4);
   l.est = o; o = align16(o + n_p * 4);
   l.best = o; o = align16(o + n_p * 8);
@@ -258,44 +270,40 @@ __device__ void compact_selection(int N, const MEState<A>& s, int np) {
   __syncthreads();
 }
 
+// Decode frame b: big arrays at `big`, per-CTA working set at `small`.
 template <int A, int SCHED, class G>
-__global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
+__device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_t b, unsigned char* big,
+                                         unsigned char* small, const int16_t* tab_int) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int16_t tab_int[256];
-  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
-  const int64_t b = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int N = a.g.N, E = a.g.E, M = a.g.M;
   const int np = a.n_p, ng = a.n_g;
-  const MELayout ly = me_layout(A, M, N, E, np, a.g.dv_max, ng);
-  unsigned char* base = smem_raw + a.graph_smem;
+  const MEBig lb = me_big(A, M, N, E);
+  const MESmall ls = me_small(N, np, a.g.dv_max, ng);
   MEState<A> s;
-  s.C = (M_*)(base + ly.C);
-  s.P = (M_*)(base + ly.P);
-  s.lam = (L_*)(base + ly.lam);
-  s.L = (L_*)(base + ly.L);
-  s.D = (D_*)(base + ly.D);
-  s.grp = (uint8_t*)(base + ly.grp);
-  s.par = (uint32_t*)(base + ly.par);
-  s.sel = (int32_t*)(base + ly.sel);
-  s.est = (int32_t*)(base + ly.est);
-  s.best = (unsigned long long*)(base + ly.best);
-  s.cnl = (int2*)(base + ly.cnl);
-  s.cand = (unsigned long long*)(base + ly.cand);
-  s.cnt = (int32_t*)(base + ly.cnt);
-  s.bits = (uint32_t*)(base + ly.bits);
-  s.misc = (MEMisc*)(base + ly.misc);
+  s.C = (M_*)(big + lb.C);
+  s.P = (M_*)(big + lb.P);
+  s.lam = (L_*)(big + lb.lam);
+  s.L = (L_*)(big + lb.L);
+  s.D = (D_*)(big + lb.D);
+  s.grp = (uint8_t*)(big + lb.grp);
+  s.par = (uint32_t*)(big + lb.par);
+  s.sel = (int32_t*)(small + ls.sel);
+  s.est = (int32_t*)(small + ls.est);
+  s.best = (unsigned long long*)(small + ls.best);
+  s.cnl = (int2*)(small + ls.cnl);
+  s.cand = (unsigned long long*)(small + ls.cand);
+  s.cnt = (int32_t*)(small + ls.cnt);
+  s.bits = (uint32_t*)(small + ls.bits);
+  s.misc = (MEMisc*)(small + ls.misc);
   s.tab = tab_int;
   MEMisc* ms = s.misc;
   const float clip = a.llr_clip;
   const uint64_t frame = a.frame_offset + (uint64_t)b;
   const int W = a.team_w, tpw = 32 / W, team = lane / W, r = lane % W;
 
-  if (A == kINT6)
-    for (int i = tid; i < 256; i += nt) tab_int[i] = a.ci_table[i];
   int bad = 0;
   for (int n = tid; n < N; n += nt) {
     L_ v;
@@ -489,11 +497,47 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
     if (a.updates) a.updates[b] = count;
     if (a.converged) a.converged[b] = ms->unsat == 0 ? 1 : 0;
   }
+  __syncthreads();
+}
+
+// Shared-memory form: CTA b decodes frame b.
+template <int A, int SCHED, class G>
+__global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int16_t tab_int[256];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  if (A == kINT6)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
+  unsigned char* big = smem_raw + a.graph_smem;
+  me_frame<A, SCHED, G>(a, g, blockIdx.x, big, big + a.smem_per_frame, tab_int);
+}
+
+// Global-memory form: CTA c owns state slot c of a.gstate and decodes frames
+// c, c + gridDim.x, ...
+template <int A, int SCHED, class G>
+__global__ void __launch_bounds__(256) me_decode_kernel_gs(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int16_t tab_int[256];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  if (A == kINT6)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
+  unsigned char* big = (unsigned char*)a.gstate + (int64_t)blockIdx.x * a.gstate_stride;
+  for (int64_t b = blockIdx.x; b < a.batch; b += gridDim.x)
+    me_frame<A, SCHED, G>(a, g, b, big, smem_raw + a.graph_smem, tab_int);
 }
 
 template <int A, int S, class G>
 cudaError_t launch_me_one(const DecodeArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame;
+  const MESmall ls = me_small(a.g.N, a.n_p, a.g.dv_max, a.n_g);
+  if (a.gstate) {
+    const size_t smem = (size_t)a.graph_smem + (size_t)ls.total;
+    auto k = me_decode_kernel_gs<A, S, G>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k<<<(unsigned)a.gstate_ctas, 256, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame + (size_t)ls.total;
   auto k = me_decode_kernel<A, S, G>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -511,8 +555,13 @@ cudaError_t launch_me_sched(const DecodeArgs& a, int sched, cudaStream_t s) {
 
 size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g) {
   (void)sched;
-  if (g.dc_max > 32) return 0;
-  return (size_t)me_layout(arith, g.M, g.N, g.E, n_p, g.dv_max, n_g).total;
+  (void)n_p;
+  (void)n_g;
+  return (size_t)me_big(arith, g.M, g.N, g.E).total;
+}
+
+size_t me_smem_per_cta(const GraphDesc& g, int n_p, int n_g) {
+  return (size_t)me_small(g.N, n_p, g.dv_max, n_g).total;
 }
 
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s) {

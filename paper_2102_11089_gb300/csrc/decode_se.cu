@@ -100,20 +100,16 @@ __device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, in
   s.Ridx[m] = (int32_t)bi;
 }
 
+// Decode frame b with its state at `base` (shared or global memory).
 template <int A, int SCHED, class G>
-__global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
+__device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_t b, unsigned char* base) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   constexpr bool kNeedR = SCHED != kLMD;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);  // all threads, before any exit
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t b = (int64_t)blockIdx.x * a.frames_per_cta + warp;
-  if (b >= a.batch) return;
+  const int lane = threadIdx.x & 31;
   const int N = a.g.N, E = a.g.E, M = a.g.M;
   const SELayout ly = se_layout(A, M, N, E, kNeedR);
-  unsigned char* base = smem_raw + a.graph_smem + (size_t)warp * ly.total;
   SEState<A> s;
   s.C = (M_*)(base + ly.C);
   s.P = (M_*)(base + ly.P);
@@ -130,6 +126,7 @@ __global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
 
   if (A == kINT6)
     for (int i = lane; i < 256; i += 32) s.tab[i] = a.ci_table[i];
+  __syncwarp();
 
   // ---- channel LLRs (coalesced) and input validation
   bool bad = false;
@@ -318,10 +315,43 @@ __global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
     if (a.updates) a.updates[b] = count;
     if (a.converged) a.converged[b] = unsat == 0 ? 1 : 0;
   }
+  __syncwarp();
+}
+
+// Shared-memory form: warp w of CTA c decodes frame c * frames_per_cta + w.
+template <int A, int SCHED, class G>
+__global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);  // all threads, before any exit
+  const int warp = threadIdx.x >> 5;
+  const int64_t b = (int64_t)blockIdx.x * a.frames_per_cta + warp;
+  if (b >= a.batch) return;
+  se_frame<A, SCHED, G>(a, g, b, smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame);
+}
+
+// Global-memory form (frame state larger than shared memory): every warp owns
+// one state slot of a.gstate and loops over the frames b = slot + k * slots.
+template <int A, int SCHED, class G>
+__global__ void __launch_bounds__(512) se_decode_kernel_gs(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  const int warp = threadIdx.x >> 5;
+  const int64_t slot = (int64_t)blockIdx.x * a.frames_per_cta + warp;
+  const int64_t slots = (int64_t)gridDim.x * a.frames_per_cta;
+  unsigned char* base = (unsigned char*)a.gstate + slot * a.gstate_stride;
+  for (int64_t b = slot; b < a.batch; b += slots) se_frame<A, SCHED, G>(a, g, b, base);
 }
 
 template <int A, int S, class G>
 cudaError_t launch_one(const DecodeArgs& a, cudaStream_t st) {
+  if (a.gstate) {
+    const size_t smem = (size_t)a.graph_smem;
+    auto k = se_decode_kernel_gs<A, S, G>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k<<<(unsigned)a.gstate_ctas, 32 * a.frames_per_cta, smem, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame * a.frames_per_cta;
   auto k = se_decode_kernel<A, S, G>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -54,6 +54,9 @@ struct DecodeArgs {
   uint64_t seed;
   uint64_t frame_offset;
   uint32_t* status;  // device status word (bit 0: bad input seen)
+  void* gstate;          // global-memory form: state slots (else null)
+  int64_t gstate_stride;  // bytes per slot
+  int32_t gstate_ctas;    // CTAs of the global-memory form
   int32_t frames_per_cta;
   int32_t smem_per_frame;
   int32_t graph_smem;    // bytes of staged graph tables at the start of shared memory
@@ -120,6 +123,7 @@ cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float*
 
 size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g);
 size_t flood_smem_per_frame(int arith, const GraphDesc& g);
-size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g);
+size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g);  // big arrays
+size_t me_smem_per_cta(const GraphDesc& g, int n_p, int n_g);  // per-CTA working set
 
 }  // namespace ldpc

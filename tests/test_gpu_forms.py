@@ -1,0 +1,88 @@
+"""Execution forms: frame state in global-memory slots (large codes, or on
+request) must give the same results as the shared-memory form and the oracle."""
+import numpy as np
+import pytest
+
+import paper_2102_11089_gb300 as L
+from paper_2102_11089_gb300 import workloads as wl
+
+from gpu_helpers import (assert_bitexact, fer_in_interval, llrs, make_code, qc, regular96, run_gpu,
+                         run_oracle, trace_prefix_ok)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ALL = ["flooding", "rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("schedule", ALL)
+def test_global_form_equals_shared_form_and_oracle(schedule):
+    spec = regular96()
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 700, 1.5, 5), 0.5)  # more frames than state slots
+    kw = dict(schedule=schedule, max_updates=6 * code.E, gamma=0.1, n_p=8, n_g=8, seed=4)
+    g_s = run_gpu(code, q, torch, arith="int6", form=L.FORM_SMEM, **kw)
+    g_g = run_gpu(code, q, torch, arith="int6", form=L.FORM_GLOBAL, **kw)
+    for k in ["hard", "updates", "converged", "llr", "trace"]:
+        assert np.array_equal(g_s[k], g_g[k]), k
+    o = run_oracle(spec, q, "int6", **kw)
+    assert_bitexact(g_g, o, schedule)
+
+
+@pytest.mark.parametrize("schedule", ["lmd-cirbp", "me-lmd-cirbp", "flooding"])
+def test_global_form_fp32_wifi(schedule):
+    spec = qc("wifi", 96)
+    code = make_code(spec)
+    lam = llrs(spec, 24, 1.75, 8)
+    kw = dict(schedule=schedule, max_updates=3 * code.E, gamma=0.1, n_p=16, n_g=16, seed=2)
+    g_s = run_gpu(code, lam, torch, arith="fp32", form=L.FORM_SMEM, **kw)
+    g_g = run_gpu(code, lam, torch, arith="fp32", form=L.FORM_GLOBAL, **kw)
+    for k in ["hard", "updates", "converged", "llr", "trace"]:
+        assert np.array_equal(g_s[k], g_g[k]), k
+
+
+@pytest.mark.parametrize("schedule,n_p", [("lmd-cirbp", 0), ("me-lmd-cirbp", 64), ("me-cirbp", 64),
+                                          ("flooding", 0)])
+def test_large_bg2_z128_int6_bitexact(schedule, n_p):
+    # n = 6656: FP32 and 6-bit state exceed one SM for the single-edge and flooding forms
+    spec = qc("bg2", 128)
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 4, 1.0, 17), 0.5)
+    kw = dict(schedule=schedule, max_updates=2 * code.E, gamma=0.1, n_p=max(n_p, 1), n_g=16, seed=6)
+    g = run_gpu(code, q, torch, arith="int6", **kw)
+    o = run_oracle(spec, q, "int6", **kw)
+    assert_bitexact(g, o, schedule)
+
+
+@pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "lmd-cirbp"])
+def test_large_bg1_z384_n26112(schedule):
+    # the 26,112-bit BG1-shaped code: frame state ~1.3 MB (FP32), global-memory form
+    spec = qc("bg1", 384)
+    code = make_code(spec)
+    assert code.N == 26112 and code.E == 122496
+    q = wl.quantize_llrs(llrs(spec, 2, 1.2, 23), 0.5)
+    kw = dict(schedule=schedule, max_updates=code.E // 2, gamma=0.1, n_p=256, n_g=16, seed=8)
+    g = run_gpu(code, q, torch, arith="int6", **kw)
+    o = run_oracle(spec, q, "int6", **kw)
+    assert_bitexact(g, o, schedule)
+    lam = llrs(spec, 2, 1.2, 23)
+    g = run_gpu(code, lam, torch, arith="fp32", **kw)
+    o = run_oracle(spec, lam, "fp32", **kw)
+    trace_prefix_ok(g, o)
+
+
+def test_shared_form_refuses_too_large_code():
+    spec = qc("bg1", 384)
+    code = make_code(spec)
+    x = torch.zeros((1, code.N), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(L.LdpcError) as e:
+        L.decode(code, x, schedule="lmd-cirbp", max_updates=10, form=L.FORM_SMEM)
+    assert e.value.name == "LDPC_ERR_UNSUPPORTED"
