@@ -136,6 +136,33 @@ def bytes_per_update(code, arith):
     return sel + commit + v2c + c2v + ci
 
 
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ["decode_me.cu", "device_math.cuh", "graph.cuh"]:
+        with open(os.path.join(ROOT, "paper_2102_11089_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(args, batch):
+    """DRAM bytes per decode launch from the committed ncu summary of this kernel
+    and workload, scaled by frames; None unless the kernel sources still match
+    the digest recorded with the capture (and the workload is the bench default)."""
+    import re
+    path = os.path.join(ROOT, "profiles", "me_decode_kernel_wifi_n2304_fp32.md")
+    if not os.path.exists(path) or args.schedule != "me-lmd-cirbp" or args.arith != "fp32" or \
+            args.n_p != 64 or args.n_g != 16 or args.ebn0 != 2.0 or args.budget_iters != 5.0:
+        return None, None
+    text = open(path).read()
+    m = re.search(r"digest \(decode_me.cu,\s+device_math.cuh, graph.cuh\): ([0-9a-f]{12})", text)
+    t = re.search(r"DRAM traffic per full bench launch \(65,536 frames, scaled by frames\): ([0-9.]+) MB", text)
+    w = re.search(r"shared wavefronts \| ([0-9.]+) G", text)
+    if not m or not t or m.group(1) != kernel_digest():
+        return None, None
+    return float(t.group(1)) * 1e6 * batch / 65536, (float(w.group(1)) if w else None)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -333,8 +360,11 @@ def run_ours(args):
     sm_count = props.multi_processor_count
     clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     smem_peak = sm_count * SMEM_BYTES_PER_CLK_PER_SM * clk_mhz * 1e6 / 1e9
+    traffic, wavefronts_g = profiled_traffic(args, B)
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                "frac": achieved / smem_peak, "traffic": None,
+                "frac": achieved / smem_peak, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch (ncu, 16,384-frame capture scaled by frames); "
+                                "the bound is shared memory, DRAM carries only LLRs in and decisions out",
                 "peak_source": f"derived: {sm_count} SMs x 128 B/clk x median SM clock "
                                f"{clk_mhz:.0f} MHz (shared memory is not in MEASURED_PEAKS)",
                 "kernel": f"me_decode_kernel ({args.schedule}, {args.arith})",
