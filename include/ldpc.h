@@ -176,6 +176,38 @@ ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batc
                           const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
                           uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);
 
+/* Decode like ldpc_decode, but without allocating any memory.  The paper has
+ * no counterpart: this is a service of the library, not a step of the method.
+ *
+ * Who needs it: callers that must not allocate at the moment they decode --
+ * for example code that runs while its stream is being captured into a CUDA
+ * graph, real-time loops that must not enter the allocator, or processes with
+ * a memory budget fixed at start-up.  ldpc_decode allocates the per-frame
+ * state slots of its global-memory form and uploads a code on its first use
+ * on a device; this entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Instead it always uses the global-memory form on one
+ * fixed device array of 32 MiB (declared static in the library, so every GPU
+ * on which the library is loaded holds it until the process exits).  Each
+ * call first copies the code's graph tables from the handle into the array
+ * (the protograph view of a lifted code is a few KB), then runs the decode
+ * with its frame-state slots after them.
+ *
+ * Arguments, outputs and results are those of ldpc_decode (params->form is
+ * ignored).  Limits and errors: LDPC_ERR_UNSUPPORTED when the graph tables
+ * plus one state slot (or, for the single-edge schedules, eight slots) do
+ * not fit in the 32 MiB; fewer slots than ldpc_decode would use otherwise.
+ * The first call on a device resolves the array's device address on that
+ * device (it must be the current device); make that first call before any
+ * stream capture.  Every call shares the one array, which keeps the contents
+ * the last call left: the kernels initialise all state they read, and the
+ * call clears its status word.  Calls that overlap on the GPU (on different
+ * streams, or from different threads) race on the array.  Non-finite or
+ * out-of-range LLRs are flagged per frame in `converged` only; ldpc_sync does
+ * not report them for this entry point. */
+ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t *code, const void *llr, int64_t batch,
+                                  const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
+                                  uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);
+
 /* Wait for `cuda_stream` and return the device status accumulated by decode
  * calls on the current device since the previous ldpc_sync (the status word
  * is then cleared): LDPC_OK, LDPC_ERR_NONFINITE_LLR, LDPC_ERR_TIMEOUT or

@@ -14,7 +14,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "LdpcError", "Code", "DecodeParams", "decode", "awgn_llr", "sync", "library_path",
+    "LdpcError", "Code", "DecodeParams", "decode", "decode_noalloc", "awgn_llr", "sync", "library_path",
     "SCHEDULES", "FLOODING", "RBP", "CIRBP", "LMD_CIRBP", "ME_CIRBP", "ME_LMD_CIRBP",
     "FP32_SUMPRODUCT", "INT6_MINSUM", "FORM_AUTO", "FORM_SMEM", "FORM_GLOBAL",
 ]
@@ -85,6 +85,7 @@ def _load():
             ("ldpc_code_edges", [P, P, P]),
             ("ldpc_awgn_llr", [P, P, I64, U64, U64, P, P, ctypes.c_float, P]),
             ("ldpc_decode", [P, P, I64, P, P, P, P, P, P, P]),
+            ("ldpc_decode_noalloc", [P, P, I64, P, P, P, P, P, P, P]),
             ("ldpc_sync", [P]),
         ]:
             f = getattr(h, name)
@@ -218,6 +219,22 @@ def decode(code: Code, llr, params: DecodeParams | None = None, *, want_trace=Fa
     _check(_load().ldpc_decode(code._h, ctypes.c_void_p(llr.data_ptr()), B, ctypes.byref(params),
                                ptr("hard"), ptr("updates"), ptr("converged"), ptr("trace"),
                                ptr("llr"), _stream_ptr(stream)))
+    return out
+
+
+def decode_noalloc(code: Code, llr, params: DecodeParams, out: dict, stream=None):
+    """ldpc_decode_noalloc: like decode(), for callers that must not allocate.
+    Every output tensor is supplied by the caller in `out` (keys hard, updates,
+    converged and optionally trace, llr); nothing is allocated, neither here nor
+    in the library, which works in its fixed 32 MiB device array."""
+    def ptr(name):
+        t = out.get(name)
+        return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+    _check(_load().ldpc_decode_noalloc(code._h, ctypes.c_void_p(llr.data_ptr()), llr.shape[0],
+                                       ctypes.byref(params), ptr("hard"), ptr("updates"),
+                                       ptr("converged"), ptr("trace"), ptr("llr"),
+                                       _stream_ptr(stream)))
     return out
 
 

@@ -289,6 +289,45 @@ void build_qc_view(ldpc_code_t* c, const int32_t* base, int32_t R, int32_t Cc, i
   c->qc_zshift = shift;
 }
 
+}  // namespace
+
+namespace ldpc {
+
+// Read-only host view of a code handle, for entry points that keep the graph in
+// memory they manage themselves.
+bool code_host_view(const void* code, CodeHostView* out) {
+  const ldpc_code_t* c = (const ldpc_code_t*)code;
+  if (!c || !out) return false;
+  out->M = c->M; out->N = c->N; out->E = c->E; out->K = c->K; out->Z = c->Z;
+  out->dv_max = c->dv_max; out->dc_max = c->dc_max; out->maxr = c->maxr;
+  // the CSR arrays are separate vectors; callers copy them one by one
+  out->tab = nullptr;
+  out->tab_words = (c->M + 1) + 3 * c->E + (c->N + 1);
+  out->qc = c->qc.empty() ? nullptr : c->qc.data();
+  out->qc_words = (int32_t)c->qc.size();
+  out->qc_R = c->qc_R; out->qc_C = c->qc_C; out->qc_nnz = c->qc_nnz;
+  out->qc_zmul = c->qc_zmul; out->qc_zshift = c->qc_zshift;
+  return true;
+}
+
+void set_error_detail(const std::string& why) { g_detail = why; }
+
+// The five CSR arrays of a code in the order of GraphDesc::tab.
+bool code_host_tab(const void* code, const int32_t* parts[5], int32_t sizes[5]) {
+  const ldpc_code_t* c = (const ldpc_code_t*)code;
+  if (!c) return false;
+  parts[0] = c->cn_ptr.data(); sizes[0] = c->M + 1;
+  parts[1] = c->e_vn.data(); sizes[1] = c->E;
+  parts[2] = c->e_cn.data(); sizes[2] = c->E;
+  parts[3] = c->vn_ptr.data(); sizes[3] = c->N + 1;
+  parts[4] = c->vn_e.data(); sizes[4] = c->E;
+  return true;
+}
+
+}  // namespace ldpc
+
+namespace {
+
 int max_optin_smem() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);

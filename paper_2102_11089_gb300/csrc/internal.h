@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include <cuda_runtime.h>
 
@@ -120,6 +121,20 @@ cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s)
 cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float* ebn0, int64_t batch,
                            uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
                            cudaStream_t s);
+
+// Host-side view of a code handle (arrays owned by the handle).
+struct CodeHostView {
+  int32_t M, N, E, K, Z;
+  int32_t dv_max, dc_max, maxr;
+  const int32_t* tab;  // cn_ptr | e_vn | e_cn | vn_ptr | vn_e
+  int32_t tab_words;
+  const int32_t* qc;   // protograph view, or null
+  int32_t qc_words, qc_R, qc_C, qc_nnz;
+  uint32_t qc_zmul, qc_zshift;
+};
+bool code_host_view(const void* code, CodeHostView* out);
+bool code_host_tab(const void* code, const int32_t* parts[5], int32_t sizes[5]);
+void set_error_detail(const std::string& why);  // text returned by ldpc_last_error_detail()
 
 size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g);
 size_t flood_smem_per_frame(int arith, const GraphDesc& g);
