@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -211,32 +212,34 @@ ldpc_status_t ensure_device(ldpc_code_t* c, const ldpc::GraphDesc** out, const u
 // reproduces the CSR maps exactly and fits the packed fields.
 void build_qc_view(ldpc_code_t* c, const int32_t* base, int32_t R, int32_t Cc, int32_t Z) {
   c->qc.clear();
-  if (R > 255 || Z > 65535 || Z <= 0) return;
-  std::vector<int32_t> rowfirst(R + 1, 0), colfirst(Cc + 1, 0), rowbase(R + 1, 0);
-  std::vector<uint32_t> rowblk, colblk;
+  if (Z <= 0) return;
+  struct Blk { int32_t r, col, s, k; };
+  std::vector<int32_t> rowbase(R + 1, 0), rowfirst(R + 1, 0), dcr(R, 0), colfirst(Cc + 1, 0), dvc(Cc, 0);
+  std::vector<Blk> rows, cols;
   std::vector<int32_t> kpos((size_t)R * Cc, -1);
   for (int32_t r = 0; r < R; ++r) {
-    rowfirst[r] = (int32_t)rowblk.size();
+    rowfirst[r] = (int32_t)rows.size();
     int32_t k = 0;
     for (int32_t col = 0; col < Cc; ++col) {
       const int32_t sft = base[(int64_t)r * Cc + col];
       if (sft < 0) continue;
-      rowblk.push_back(((uint32_t)col << 16) | (uint32_t)sft);
+      rows.push_back({r, col, sft, k});
       kpos[(size_t)r * Cc + col] = k++;
     }
-    if (k > 255) return;
+    dcr[r] = k;
+    if ((int64_t)rowbase[r] + (int64_t)k * Z > 0x7fffffff) return;
     rowbase[r + 1] = rowbase[r] + k * Z;
   }
-  rowfirst[R] = (int32_t)rowblk.size();
+  rowfirst[R] = (int32_t)rows.size();
   for (int32_t col = 0; col < Cc; ++col) {
-    colfirst[col] = (int32_t)colblk.size();
+    colfirst[col] = (int32_t)cols.size();
     for (int32_t r = 0; r < R; ++r) {
       const int32_t sft = base[(int64_t)r * Cc + col];
-      if (sft < 0) continue;
-      colblk.push_back(((uint32_t)r << 24) | ((uint32_t)kpos[(size_t)r * Cc + col] << 16) | (uint32_t)sft);
+      if (sft >= 0) cols.push_back({r, col, sft, kpos[(size_t)r * Cc + col]});
     }
+    dvc[col] = (int32_t)cols.size() - colfirst[col];
   }
-  colfirst[Cc] = (int32_t)colblk.size();
+  colfirst[Cc] = (int32_t)cols.size();
   // n / Z == umulhi(n, mul) >> shift for every n < max(R, C) Z
   const uint32_t limit = (uint32_t)std::max(R, Cc) * (uint32_t)Z;
   uint32_t mul = 0, shift = 0;
@@ -255,36 +258,38 @@ void build_qc_view(ldpc_code_t* c, const int32_t* base, int32_t R, int32_t Cc, i
     }
   }
   if (!found) return;
-  // self-check: the view must give the CSR edge ids and neighbours
+  // self-check with the kernels' formulas: the view must give the CSR ids and neighbours
   for (int32_t m = 0; m < c->M; ++m) {
-    const int32_t r = m / Z, z = m % Z, dc = rowfirst[r + 1] - rowfirst[r];
-    if (c->cn_ptr[m] != rowbase[r] + z * dc || c->cn_ptr[m + 1] - c->cn_ptr[m] != dc) return;
+    const int32_t r = m / Z, z = m - r * Z, dc = dcr[r];
+    const int32_t b = rowbase[r] + z * dc;
+    if (c->cn_ptr[m] != b || c->cn_ptr[m + 1] - c->cn_ptr[m] != dc) return;
     for (int32_t k = 0; k < dc; ++k) {
-      const uint32_t blk = rowblk[rowfirst[r] + k];
-      const int32_t n = (int32_t)(blk >> 16) * Z + (z + (int32_t)(blk & 0xffffu)) % Z;
-      if (c->e_vn[c->cn_ptr[m] + k] != n) return;
+      const Blk& bb = rows[rowfirst[r] + k];
+      int32_t zz = z + bb.s;
+      zz -= zz >= Z ? Z : 0;
+      if (zz < 0 || zz >= Z || c->e_vn[b + k] != bb.col * Z + zz) return;
     }
   }
   for (int32_t n = 0; n < c->N; ++n) {
-    const int32_t col = n / Z, z = n % Z, dv = colfirst[col + 1] - colfirst[col];
-    if (c->vn_ptr[n + 1] - c->vn_ptr[n] != dv) return;
-    for (int32_t k = 0; k < dv; ++k) {
-      const uint32_t blk = colblk[colfirst[col] + k];
-      const int32_t r = (int32_t)(blk >> 24), kk = (int32_t)((blk >> 16) & 255u), sft = (int32_t)(blk & 0xffffu);
-      const int32_t zz = ((z - sft) % Z + Z) % Z;
-      const int32_t dc = rowfirst[r + 1] - rowfirst[r];
-      const int32_t e = rowbase[r] + zz * dc + kk;
-      if (c->vn_e[c->vn_ptr[n] + k] != e || c->e_cn[e] != r * Z + zz) return;
+    const int32_t col = n / Z, z = n - col * Z;
+    if (c->vn_ptr[n + 1] - c->vn_ptr[n] != dvc[col]) return;
+    for (int32_t k = 0; k < dvc[col]; ++k) {
+      const Blk& bb = cols[colfirst[col] + k];
+      int32_t zz = z - bb.s;
+      zz += zz < 0 ? Z : 0;
+      if (zz < 0 || zz >= Z) return;
+      const int32_t e = rowbase[bb.r] + bb.k + zz * dcr[bb.r];
+      if (c->vn_e[c->vn_ptr[n] + k] != e || c->e_cn[e] != bb.r * Z + zz) return;
     }
   }
-  c->qc.insert(c->qc.end(), rowbase.begin(), rowbase.end());
-  c->qc.insert(c->qc.end(), rowfirst.begin(), rowfirst.end());
-  c->qc.insert(c->qc.end(), colfirst.begin(), colfirst.end());
-  for (uint32_t v : rowblk) c->qc.push_back((int32_t)v);
-  for (uint32_t v : colblk) c->qc.push_back((int32_t)v);
+  std::vector<int32_t>& q = c->qc;
+  for (int32_t r = 0; r < R; ++r) q.insert(q.end(), {rowbase[r], rowfirst[r], dcr[r], r * Z});
+  for (int32_t col = 0; col < Cc; ++col) q.insert(q.end(), {colfirst[col], dvc[col], col * Z, 0});
+  for (const Blk& bb : cols) q.insert(q.end(), {bb.s, bb.r * Z, rowbase[bb.r] + bb.k, dcr[bb.r]});
+  for (const Blk& bb : rows) q.insert(q.end(), {bb.col * Z, bb.s});
   c->qc_R = R;
   c->qc_C = Cc;
-  c->qc_nnz = (int32_t)rowblk.size();
+  c->qc_nnz = (int32_t)rows.size();
   c->qc_zmul = mul;
   c->qc_zshift = shift;
 }
@@ -526,6 +531,10 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   a.graph_smem = ldpc::graph_smem_bytes(*g);
   a.team_w = 1;
   while (a.team_w < g->dc_max) a.team_w <<= 1;
+  // multi-edge CTA size: FP32 frames run two CTAs per SM (shared memory), where 512
+  // threads hide more latency; 6-bit frames run four 256-thread CTAs per SM
+  a.cta_threads = p->arith == LDPC_INT6_MINSUM ? 256 : 512;
+  if (const char* t = std::getenv("LDPC_ME_THREADS")) a.cta_threads = std::atoi(t) == 512 ? 512 : 256;
   if (p->arith == LDPC_INT6_MINSUM)
     for (int q = -127; q <= 127; ++q)
       a.ci_table[q + 127] = (int16_t)std::round(32767.0 * std::tanh(q * (double)p->q_step / 2.0));

@@ -24,7 +24,7 @@ namespace ldpc {
 
 namespace {
 
-constexpr int kCap = 1024;  // candidate list of the random fill
+constexpr int kCap = 512;  // candidate list of the random fill
 
 // Big per-frame arrays (shared memory, or a global-memory slot for large codes)
 struct MEBig {
@@ -32,7 +32,7 @@ struct MEBig {
 };
 // Per-CTA working set of one step (always shared memory)
 struct MESmall {
-  int sel, est, best, cnl, cand, cnt, bits, misc, total;
+  int sel, est, best, excl, cnl, cand, cnt, cntS, bits, touched, misc, total;
 };
 
 __host__ __device__ inline MEBig me_big(int arith, int M, int N, int E) {
@@ -58,10 +58,13 @@ __host__ __device__ inline MESmall me_small(int N, int n_p, int dvm, int n_g) {
   l.sel = o; o = align16(o + n_p * 4);
   l.est = o; o = align16(o + n_p * 4);
   l.best = o; o = align16(o + n_p * 8);
+  l.excl = o; o = align16(o + n_p * 4);
   l.cnl = o; o = align16(o + n_p * (dvm > 1 ? dvm - 1 : 1) * 8);
   l.cand = o; o = align16(o + kCap * 8);
   l.cnt = o; o = align16(o + n_g * 4);
+  l.cntS = o; o = align16(o + n_g * 4);
   l.bits = o; o = align16(o + ((N + 31) / 32) * 4);
+  l.touched = o; o = align16(o + ((N + 31) / 32) * 4);
   l.misc = o; o = align16(o + 32 * 4);
   l.total = o;
   return l;
@@ -73,7 +76,7 @@ struct MEMisc {
   int ncn;   // affected checks this step
   int nsel;  // selected VNs
   int npp;   // |P'| (ME-LMD)
-  int kstar, fill_g, need, sz;
+  int kstar, fill_g, need, top;
   int ncand;
   uint32_t thr, lo, hi;
   int done, hi_set;
@@ -94,10 +97,13 @@ struct MEState {
   int32_t* sel;
   int32_t* est;
   unsigned long long* best;
+  int32_t* excl;   // P' of ME-LMD-CIRBP (excluded from Algorithm 4's top-up)
   int2* cnl;  // (check, owner k)
   unsigned long long* cand;
-  int32_t* cnt;
+  int32_t* cnt;    // |G_i| over all VNs, kept up to date with grp
+  int32_t* cntS;   // per-group count of the VNs excluded from Algorithm 4's search set
   uint32_t* bits;  // selection bitmap over VNs
+  uint32_t* touched;  // VNs whose D was rewritten in this step
   MEMisc* misc;
   const int16_t* tab;
 };
@@ -127,79 +133,97 @@ __device__ __forceinline__ int group_of(uint16_t d, int ng) { return min((int)((
 
 __device__ __forceinline__ bool in_bits(const uint32_t* bits, int n) { return (bits[n >> 5] >> (n & 31)) & 1u; }
 
-// Algorithm 4 over S = {n : bit n of s.bits clear}: sets the bits of the
-// selected VNs (at most np of them).  All threads call it.
+// Algorithm 4 over S = O_N minus nexcl excluded VNs (their bits are set and
+// s.cntS counts them per group): sets the bits of the selected VNs (at most
+// np).  Group sizes come from the maintained s.cnt.  All threads call it.
 template <int A>
-__device__ void alg4(const MEState<A>& s, int N, int np, int ng, uint32_t step, uint64_t frame, uint64_t seed) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+__device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint32_t step, uint64_t frame,
+                     uint64_t seed) {
+  const int tid = threadIdx.x, nt = blockDim.x;
   MEMisc* ms = s.misc;
-  for (int i = tid; i < ng; i += nt) s.cnt[i] = 0;
-  if (tid == 0) ms->sz = 0;
-  __syncthreads();
-  int my = 0;
-  for (int n = tid; n < N; n += nt) {  // line 2: |G_i|
-    if (in_bits(s.bits, n)) continue;
-    atomicAdd(&s.cnt[s.grp[n]], 1);
-    ++my;
-  }
-  my = __reduce_add_sync(kFull, my);
-  if (lane == 0 && my) atomicAdd(&ms->sz, my);
-  __syncthreads();
-  if (tid == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P}
+  if ((tid >> 5) == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S (one warp)
+    // |G_i| over S = cnt[i] - cntS[i] (cntS counts the excluded VNs per group);
+    // lane l of chunk b looks at group ng - 1 - (b + l), i.e. k = b + l + 1
+    const int lane = tid & 31;
+    const int sz = N - nexcl;
     int kstar = 0, q = 0;
-    if (ms->sz <= np) {
+    if (sz <= np) {
       kstar = ng;
-      q = ms->sz;
+      q = sz;
     } else {
-      for (int k = 1; k < ng; ++k) {
-        if (q + s.cnt[ng - k] > np) break;
-        q += s.cnt[ng - k];
-        kstar = k;
+      for (int b0 = 0; b0 < ng - 1; b0 += 32) {
+        const int i = b0 + lane;
+        const int c = i < ng - 1 ? s.cnt[ng - 1 - i] - s.cntS[ng - 1 - i] : np + 1;  // > np, no overflow
+        int pre = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, pre, o);
+          if (lane >= o) pre += y;
+        }
+        const unsigned ok = __ballot_sync(kFull, q + pre <= np);  // a prefix of the lanes
+        const int nok = __popc(ok);
+        kstar += nok;
+        q += nok > 0 ? __shfl_sync(kFull, pre, nok - 1) : 0;
+        if (nok < 32) break;
       }
     }
-    const int need = kstar < ng ? np - q : 0;
-    ms->kstar = kstar;
-    ms->need = need;
-    ms->fill_g = ng - kstar - 1;
-    ms->thr = 0xffffffffu;
-    if (need > 0) {
-      const int members = s.cnt[ng - kstar - 1];
-      const unsigned long long want = (unsigned long long)(3 * need / 2 + 48);
-      if (members > kCap / 2)
-        ms->thr = (uint32_t)min(0xffffffffull, (want << 32) / (unsigned long long)members);
+    if (lane == 0) {
+      const int need = kstar < ng ? np - q : 0;
+      ms->kstar = kstar;
+      ms->top = ng - kstar;
+      ms->need = need;
+      ms->fill_g = ng - kstar - 1;
+      ms->thr = 0xffffffffu;
+      if (need > 0) {
+        const int fg = ng - kstar - 1;
+        const int members = s.cnt[fg] - s.cntS[fg];
+        const unsigned long long want = (unsigned long long)(3 * need / 2 + 48);
+        if (members > kCap / 2)
+          ms->thr = (uint32_t)min(0xffffffffull, (want << 32) / (unsigned long long)members);
+      }
+      ms->lo = 0;
+      ms->hi = 0xffffffffu;
+      ms->hi_set = 0;
+      ms->done = need == 0;
+      ms->ncand = 0;
     }
-    ms->lo = 0;
-    ms->hi = 0xffffffffu;
-    ms->hi_set = 0;
-    ms->done = need == 0;
-    ms->ncand = 0;
   }
   __syncthreads();
-  const int top = ng - ms->kstar, fg = ms->fill_g, need = ms->need;
-  // lines 4-6: the `need` fill-group members with the smallest keys
+  const int top = ms->top, fg = ms->fill_g, need = ms->need;
+  const int nq = (N + 3) / 4;
+  const uint32_t* grp4 = (const uint32_t*)s.grp;
+  // one pass over VN quads: line 3 selects Q(k*); lines 4-6 gather fill candidates
+  // (key = word i of the Philox block of quad q)
   for (int iter = 0; iter < 64; ++iter) {
-    if (ms->done) break;  // uniform: written by thread 0 before a barrier
     const uint32_t thr = ms->thr;
-    for (int q = tid; q < (N + 3) / 4; q += nt) {
-      unsigned mem = 0;
+    const bool fill = !ms->done;
+    for (int q = tid; q < nq; q += nt) {
+      const uint32_t g4 = grp4[q];
+      const unsigned ex = (s.bits[q >> 3] >> ((q & 7) * 4)) & 0xfu;
+      unsigned fm = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int n = 4 * q + i;
-        if (n < N && !in_bits(s.bits, n) && s.grp[n] == fg) mem |= 1u << i;
+        if (n >= N || ((ex >> i) & 1u)) continue;
+        const int gi = (int)((g4 >> (8 * i)) & 0xffu);
+        if (iter == 0 && gi >= top) atomicOr(&s.bits[n >> 5], 1u << (n & 31));
+        if (gi == fg) fm |= 1u << i;
       }
-      if (!mem) continue;
+      if (!fill || !fm) continue;
       uint32_t w[4] = {(uint32_t)q, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
       philox4(w, seed);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (!((mem >> i) & 1u) || w[i] > thr) continue;
+        if (!((fm >> i) & 1u) || w[i] > thr) continue;
         const int pos = atomicAdd(&ms->ncand, 1);
         if (pos < kCap) s.cand[pos] = ((unsigned long long)w[i] << 32) | (unsigned)(4 * q + i);
       }
     }
     __syncthreads();
+    if (!fill) break;
     const int nc = ms->ncand;
-    if (nc >= need && nc <= kCap) {
+    const bool ok = nc >= need && nc <= kCap;
+    if (ok) {
       // exact rank among the candidates: (key, n) is unique
       for (int c = tid; c < nc; c += nt) {
         const unsigned long long kc = s.cand[c];
@@ -213,7 +237,7 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, uint32_t step, 
     }
     __syncthreads();
     if (tid == 0) {
-      if (nc >= need && nc <= kCap) {
+      if (ok) {
         ms->done = 1;
       } else if (nc < need) {  // bisect the threshold upwards
         ms->lo = thr;
@@ -227,19 +251,14 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, uint32_t step, 
       ms->ncand = 0;
     }
     __syncthreads();
+    if (ms->done) break;
   }
-  // line 3: P = Q(k*) (groups >= N_G - k*)
-  for (int n = tid; n < N; n += nt) {
-    if (s.grp[n] < top || in_bits(s.bits, n)) continue;
-    atomicOr(&s.bits[n >> 5], 1u << (n & 31));
-  }
-  __syncthreads();
 }
 
-// Compact the selection bitmap into s.sel (ascending) and clear it.
+// Compact the selection bitmap into s.sel (ascending); the next step clears it.
 template <int A>
 __device__ void compact_selection(int N, const MEState<A>& s, int np) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int words = (N + 31) / 32;
   if (warp == 0) {
     int base = 0;
@@ -263,10 +282,12 @@ __device__ void compact_selection(int N, const MEState<A>& s, int np) {
       }
       base += __shfl_sync(kFull, incl, 31);
     }
-    if (lane == 0) s.misc->nsel = min(base, np);
+    if (lane == 0) {
+      s.misc->nsel = min(base, np);
+      s.misc->ncn = 0;
+      s.misc->npp = 0;
+    }
   }
-  __syncthreads();
-  for (int w = tid; w < words; w += nt) s.bits[w] = 0u;
   __syncthreads();
 }
 
@@ -293,10 +314,13 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   s.sel = (int32_t*)(small + ls.sel);
   s.est = (int32_t*)(small + ls.est);
   s.best = (unsigned long long*)(small + ls.best);
+  s.excl = (int32_t*)(small + ls.excl);
   s.cnl = (int2*)(small + ls.cnl);
   s.cand = (unsigned long long*)(small + ls.cand);
   s.cnt = (int32_t*)(small + ls.cnt);
+  s.cntS = (int32_t*)(small + ls.cntS);
   s.bits = (uint32_t*)(small + ls.bits);
+  s.touched = (uint32_t*)(small + ls.touched);
   s.misc = (MEMisc*)(small + ls.misc);
   s.tab = tab_int;
   MEMisc* ms = s.misc;
@@ -322,7 +346,15 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   for (int e = tid; e < E; e += nt) s.C[e] = (M_)0;
   for (int w = tid; w < (N + 31) / 32; w += nt) s.bits[w] = 0u;
   for (int w = tid; w < (M + 31) / 32; w += nt) s.par[w] = 0u;
-  if (tid == 0) ms->unsat = 0;
+  for (int i = tid; i < ng; i += nt) {
+    s.cnt[i] = 0;
+    s.cntS[i] = 0;
+  }
+  if (tid == 0) {
+    ms->unsat = 0;
+    ms->ncn = 0;
+    ms->npp = 0;
+  }
   if (__syncthreads_or(bad)) {
     for (int n = tid; n < N; n += nt) {
       if (a.hard) a.hard[b * N + n] = 0;
@@ -353,8 +385,10 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   for (int n = tid; n < N; n += nt) {
     const L_ lt = vn_total<A, G>(g, s.lam, s.P, n);
     const D_ d = ci_me(s, s.L[n], lt);
+    const int gi = group_of(d, ng);
     s.D[n] = d;
-    s.grp[n] = (uint8_t)group_of(d, ng);
+    s.grp[n] = (uint8_t)gi;
+    atomicAdd(&s.cnt[gi], 1);
   }
   __syncthreads();
 
@@ -362,14 +396,21 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   uint32_t step = 0;
   bool stop = a.check_interval > 0 && ms->unsat == 0;
   if (!stop && a.max_updates > 0) {  // Alg. 5 line 4 / Alg. 6 line 4
-    alg4<A>(s, N, np, ng, step, frame, a.seed);
+    alg4<A>(s, N, np, ng, 0, step, frame, a.seed);
     compact_selection<A>(N, s, np);
   }
   while (!stop && count < a.max_updates) {
     int nsel = ms->nsel;
     if (nsel <= 0) break;  // nothing selectable: the step would not advance
     if ((int64_t)nsel > a.max_updates - count) nsel = (int)(a.max_updates - count);
-    // -- m*_p = argmax_i R_{i->p}, i in M(p), on the pre-step state
+    // -- for each selected p: m*_p = argmax_i R_{i->p} on the pre-step state (the
+    //    edges of p are disjoint from every other p's), commit L^C <- L~^C, L_p,
+    //    syndrome, trace, the checks i in M(p)\m*_p whose inputs changed
+    for (int w = tid; w < (N + 31) / 32; w += nt) {
+      s.bits[w] = 0u;
+      s.touched[w] = 0u;
+    }
+    for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     for (int k = tid; k < nsel; k += nt) {
       const int p = s.sel[k];
       const typename G::V v = g.vn(p);
@@ -379,20 +420,14 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
         g.vedge(v, q, e, m);
         am_update(bk, bi, rkey(s.P[e], s.C[e]), (uint32_t)e);
       }
-      s.est[k] = (int)bi;
+      const int es = (int)bi;
+      s.est[k] = es;
       s.best[k] = 0ull;
-    }
-    if (tid == 0) ms->ncn = 0;
-    __syncthreads();
-    // -- commits, L_p, syndrome, trace, affected checks i in M(p)\m*_p
-    for (int k = tid; k < nsel; k += nt) {
-      const int p = s.sel[k], es = s.est[k];
       s.C[es] = s.P[es];
       const L_ lold = s.L[p];
       const L_ lnew = vn_total<A, G>(g, s.lam, s.C, p);
       s.L[p] = lnew;
       const bool flip = (lold < (L_)0) != (lnew < (L_)0);
-      const typename G::V v = g.vn(p);
       for (int q = 0; q < v.d; ++q) {
         int e, m;
         g.vedge(v, q, e, m);
@@ -419,7 +454,23 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
       if (r < dc) s.P[e] = out;
     }
     __syncthreads();
-    // -- L~_j, D_j next to affected checks (and of every p); LMD candidates
+    // -- L~_j, D_j next to affected checks and of every p; the first writer of a
+    //    VN in this step updates its group and the group sizes; LMD candidates
+    auto refresh_vn = [&](int j) -> D_ {
+      const L_ lt = vn_total<A, G>(g, s.lam, s.P, j);
+      const D_ d = ci_me(s, s.L[j], lt);
+      const uint32_t bit = 1u << (j & 31);
+      if (!(atomicOr(&s.touched[j >> 5], bit) & bit)) {
+        s.D[j] = d;
+        const int gn = group_of(d, ng), go = s.grp[j];
+        if (gn != go) {
+          s.grp[j] = (uint8_t)gn;
+          atomicSub(&s.cnt[go], 1);
+          atomicAdd(&s.cnt[gn], 1);
+        }
+      }
+      return d;
+    };
     for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
       const int t = t0 + team;
       if (t >= ncn) continue;
@@ -427,22 +478,13 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
       const typename G::C cc = g.cn(ck.x);
       if (r >= cc.d) continue;
       const int j = g.cvn(cc, r);
-      const L_ lt = vn_total<A, G>(g, s.lam, s.P, j);
-      const D_ d = ci_me(s, s.L[j], lt);
-      s.D[j] = d;
-      s.grp[j] = (uint8_t)group_of(d, ng);
+      const D_ d = refresh_vn(j);
       if (SCHED == kMELMD && j != s.sel[ck.y]) {
         const unsigned long long key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
         atomicMax(&s.best[ck.y], key);
       }
     }
-    for (int k = tid; k < nsel; k += nt) {
-      const int p = s.sel[k];
-      const L_ lt = vn_total<A, G>(g, s.lam, s.P, p);
-      const D_ d = ci_me(s, s.L[p], lt);
-      s.D[p] = d;
-      s.grp[p] = (uint8_t)group_of(d, ng);
-    }
+    for (int k = tid; k < nsel; k += nt) refresh_vn(s.sel[k]);
     __syncthreads();
     count += nsel;
     ++step;
@@ -450,42 +492,37 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
         ms->unsat == 0)
       break;
     if (count >= a.max_updates) break;
-    if (SCHED == kMECIRBP) {
-      alg4<A>(s, N, np, ng, step, frame, a.seed);  // Alg. 5 line 4
+    if (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
+      alg4<A>(s, N, np, ng, 0, step, frame, a.seed);  // Alg. 5 line 4
       compact_selection<A>(N, s, np);
       continue;
     }
-    // -- Alg. 6 lines 6-10: P' = {argmax_{j in U(m*_p, p)} D_j}; degree-1 rule (Sec. 5.A)
+    // -- Alg. 6 lines 6-10: P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of
+    //    Sec. 5.A: N(m*_p)\p), de-duplicated in the selection bitmap
     for (int k = tid; k < nsel; k += nt) {
       const int p = s.sel[k];
+      unsigned long long bk = s.best[k];
       if (g.vn(p).d == 1) {
         const typename G::C cc = g.cn(g.ecn(s.est[k]));
-        unsigned long long bk = 0ull;
+        bk = 0ull;
         for (int q = 0; q < cc.d; ++q) {
           const int j = g.cvn(cc, q);
           if (j == p) continue;
           const unsigned long long key = ((unsigned long long)mkey(s.D[j]) << 32) | (0xffffffffu - (uint32_t)j);
           bk = key > bk ? key : bk;
         }
-        s.best[k] = bk;
       }
-    }
-    if (tid == 0) ms->npp = 0;
-    __syncthreads();
-    int mine = 0;
-    for (int k = tid; k < nsel; k += nt) {
-      const unsigned long long bk = s.best[k];
       if (bk == 0ull) continue;  // empty candidate set
       const int j = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
       const uint32_t bit = 1u << (j & 31);
-      const uint32_t old = atomicOr(&s.bits[j >> 5], bit);
-      mine += (old & bit) ? 0 : 1;
+      if (!(atomicOr(&s.bits[j >> 5], bit) & bit)) {
+        s.excl[atomicAdd(&ms->npp, 1)] = j;
+        atomicAdd(&s.cntS[s.grp[j]], 1);  // per-group count of P' for Algorithm 4's top-up
+      }
     }
-    mine = __reduce_add_sync(kFull, mine);
-    if (lane == 0 && mine) atomicAdd(&ms->npp, mine);
     __syncthreads();
     const int npp = ms->npp;
-    if (npp < np) alg4<A>(s, N, np - npp, ng, step, frame, a.seed);  // lines 11-13
+    if (npp < np) alg4<A>(s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
     compact_selection<A>(N, s, np);
   }
 
@@ -500,9 +537,17 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   __syncthreads();
 }
 
+// Registers: FP32 frames are limited to two CTAs per SM by shared memory, so two
+// resident CTAs are requested (up to 128 registers at 256 threads, 64 at 512);
+// 6-bit frames fit more CTAs: four of 256 threads or two of 512 (64 registers).
+template <int A, int TPB>
+struct MEBounds {
+  static constexpr int kMinBlocks = A == kFP32 ? 2 : (TPB == 256 ? 4 : 2);
+};
+
 // Shared-memory form: CTA b decodes frame b.
-template <int A, int SCHED, class G>
-__global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
+template <int A, int SCHED, class G, int TPB>
+__global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_kernel(const DecodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int16_t tab_int[256];
   const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
@@ -514,8 +559,8 @@ __global__ void __launch_bounds__(256) me_decode_kernel(const DecodeArgs a) {
 
 // Global-memory form: CTA c owns state slot c of a.gstate and decodes frames
 // c, c + gridDim.x, ...
-template <int A, int SCHED, class G>
-__global__ void __launch_bounds__(256) me_decode_kernel_gs(const DecodeArgs a) {
+template <int A, int SCHED, class G, int TPB>
+__global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_kernel_gs(const DecodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int16_t tab_int[256];
   const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
@@ -526,23 +571,28 @@ __global__ void __launch_bounds__(256) me_decode_kernel_gs(const DecodeArgs a) {
     me_frame<A, SCHED, G>(a, g, b, big, smem_raw + a.graph_smem, tab_int);
 }
 
-template <int A, int S, class G>
-cudaError_t launch_me_one(const DecodeArgs& a, cudaStream_t st) {
+template <int A, int S, class G, int TPB>
+cudaError_t launch_me_tpb(const DecodeArgs& a, cudaStream_t st) {
   const MESmall ls = me_small(a.g.N, a.n_p, a.g.dv_max, a.n_g);
   if (a.gstate) {
     const size_t smem = (size_t)a.graph_smem + (size_t)ls.total;
-    auto k = me_decode_kernel_gs<A, S, G>;
+    auto k = me_decode_kernel_gs<A, S, G, TPB>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k<<<(unsigned)a.gstate_ctas, 256, smem, st>>>(a);
+    k<<<(unsigned)a.gstate_ctas, TPB, smem, st>>>(a);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame + (size_t)ls.total;
-  auto k = me_decode_kernel<A, S, G>;
+  auto k = me_decode_kernel<A, S, G, TPB>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k<<<(unsigned)a.batch, 256, smem, st>>>(a);
+  k<<<(unsigned)a.batch, TPB, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int A, int S, class G>
+cudaError_t launch_me_one(const DecodeArgs& a, cudaStream_t st) {
+  return a.cta_threads == 512 ? launch_me_tpb<A, S, G, 512>(a, st) : launch_me_tpb<A, S, G, 256>(a, st);
 }
 
 template <int A, class G>

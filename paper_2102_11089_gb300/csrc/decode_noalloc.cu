@@ -157,6 +157,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   a.graph_smem = ldpc::graph_smem_bytes(g);
   a.team_w = 1;
   while (a.team_w < g.dc_max) a.team_w <<= 1;
+  a.cta_threads = p->arith == LDPC_INT6_MINSUM ? 256 : 512;
   const int arith = p->arith == LDPC_INT6_MINSUM ? ldpc::kINT6 : ldpc::kFP32;
   if (arith == ldpc::kINT6)
     for (int q = -127; q <= 127; ++q)

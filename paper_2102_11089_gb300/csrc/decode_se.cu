@@ -11,7 +11,7 @@
 //     exclude-one C2V of eq. (2) (or min-sum) by width-W shuffles, then
 //     L~_j and D_j (eq. 8) of j in N(i)\n*, which are also the LMD candidates.
 // Per-frame state in shared memory:
-//   C[E] L^C, P[E] L~^C, lam/L/Lt[N], D[N], Rmax/Ridx[M] (largest residual per
+//   C[E] L^C, P[E] L~^C, lam/L[N], D[N], Rmax/Ridx[M] (largest residual per
 //   check, for the global argmax of eq. (5): RBP and CIRBP's fallback), par
 //   (syndrome bits of the tentative decisions bsgn(L), Sec. 2.A).
 // The graph is a QCGraph (protograph arithmetic) or TabGraph (CSR tables), both
@@ -31,7 +31,6 @@ struct SEState {
   M_* P;
   L_* lam;
   L_* L;
-  L_* Lt;
   D_* D;
   M_* Rmax;
   int32_t* Ridx;
@@ -44,13 +43,17 @@ __device__ __forceinline__ uint16_t ci_val(const SEState<kINT6>& s, int a, int b
   return ci_int(a, b, s.tab);
 }
 
-template <int A>
-__device__ __forceinline__ typename Arith<A>::llr warp_sum_llr(typename Arith<A>::llr v);
-template <>
-__device__ __forceinline__ float warp_sum_llr<kFP32>(float v) { return warp_sum_f(v); }
-template <>
-__device__ __forceinline__ int16_t warp_sum_llr<kINT6>(int16_t v) {
-  return (int16_t)__reduce_add_sync(kFull, (int)v);
+// two warp sums at once (independent butterflies interleave)
+__device__ __forceinline__ void warp_sum2(float& a, float& b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    b += __shfl_xor_sync(kFull, b, o);
+  }
+}
+__device__ __forceinline__ void warp_sum2(int16_t& a, int16_t& b) {
+  a = (int16_t)__reduce_add_sync(kFull, (int)a);
+  b = (int16_t)__reduce_add_sync(kFull, (int)b);
 }
 
 // argmax over D of every VN, lowest index on ties (Alg. 1 line 4)
@@ -115,7 +118,6 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
   s.P = (M_*)(base + ly.P);
   s.lam = (L_*)(base + ly.lam);
   s.L = (L_*)(base + ly.L);
-  s.Lt = (L_*)(base + ly.Lt);
   s.D = (D_*)(base + ly.D);
   s.Rmax = (M_*)(base + ly.Rmax);
   s.Ridx = (int32_t*)(base + ly.Ridx);
@@ -168,11 +170,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
     if (r < dc) s.P[e] = out;
   }
   __syncwarp();
-  for (int n = lane; n < N; n += 32) {
-    const L_ lt = vn_total<A, G>(g, s.lam, s.P, n);
-    s.Lt[n] = lt;
-    s.D[n] = ci_val(s, s.L[n], lt);
-  }
+  for (int n = lane; n < N; n += 32) s.D[n] = ci_val(s, s.L[n], vn_total<A, G>(g, s.lam, s.P, n));
   uint32_t unsat = 0;
   for (int m0 = 0; m0 < M; m0 += 32) {
     const int m = m0 + lane;
@@ -217,10 +215,13 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
     const typename G::V vv = g.vn(nstar);
     const int dv = vv.d;
     int my_e = 0, my_m = -1;
+    M_ my_p = (M_)0, my_c = (M_)0;
     uint32_t rk = 0, ri = 0xffffffffu;
     if (lane < dv) {
       g.vedge(vv, lane, my_e, my_m);
-      rk = rkey(s.P[my_e], s.C[my_e]);
+      my_p = s.P[my_e];
+      my_c = s.C[my_e];
+      rk = rkey(my_p, my_c);
       ri = (uint32_t)my_e;
     }
     uint32_t kk;
@@ -229,17 +230,27 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
     const int kstar = __ffs(own) - 1;
     const int mstar = __shfl_sync(kFull, my_m, kstar);
 
-    // -- commit (Alg. 1 line 9): L^C <- L~^C, update L_{n*}
+    // -- commit (Alg. 1 line 9): L^C <- L~^C, update L_{n*}; L~_{n*} is unchanged
+    //    by the commit and is summed alongside for D_{n*}
     const L_ Lold = s.L[nstar];
-    L_ part = (L_)0;
-    if (lane < dv) part = (L_)((lane == kstar) ? s.P[my_e] : s.C[my_e]);
-    if (A == kFP32 && lane == 0) part = (L_)(part + s.lam[nstar]);
-    L_ Lnew = warp_sum_llr<A>(part);
-    if (A == kINT6) Lnew = (L_)(Lnew + s.lam[nstar]);
-    if (lane == kstar) s.C[estar] = s.P[estar];
+    L_ Lnew = (L_)0, Ltn = (L_)0;
+    if (lane < dv) {
+      Lnew = (L_)(lane == kstar ? my_p : my_c);
+      Ltn = (L_)my_p;
+    }
+    if (A == kFP32 && lane == 0) {
+      Lnew = (L_)(Lnew + s.lam[nstar]);
+      Ltn = (L_)(Ltn + s.lam[nstar]);
+    }
+    warp_sum2(Lnew, Ltn);
+    if (A == kINT6) {
+      Lnew = (L_)(Lnew + s.lam[nstar]);
+      Ltn = (L_)(Ltn + s.lam[nstar]);
+    }
+    if (lane == kstar) s.C[estar] = my_p;
     if (lane == 0) {
       s.L[nstar] = Lnew;
-      s.D[nstar] = ci_val(s, Lnew, s.Lt[nstar]);  // reading: D of n* follows L_{n*}
+      s.D[nstar] = ci_val(s, Lnew, Ltn);  // reading: D of n* follows L_{n*}
     }
     if ((Lold < (L_)0) != (Lnew < (L_)0)) {  // tentative decision flipped
       int delta = 0;
@@ -253,33 +264,49 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
     if (lane == 0 && a.trace) a.trace[b * a.max_updates + count] = estar;
     __syncwarp();
 
-    // -- refresh (Alg. 1 lines 10-13): team i handles the i-th check of M(n*)\m*
+    // -- refresh (Alg. 1 lines 10-13): team i handles the i-th check of M(n*)\m*:
+    //    new V2C inputs and precomputed C2V (eq. 2), then L~_j and D_j of its
+    //    variables j != n* (also the LMD candidates)
     const int nref = dv - 1;
-    for (int i0 = 0; i0 < nref; i0 += tpw) {
-      const int i = i0 + team;
-      const int k = i < kstar ? i : i + 1;
+    uint32_t ck = 0, cidx = 0xffffffffu;
+    if (nref <= tpw) {  // one pass of teams
+      const int k = team < kstar ? team : team + 1;
       const int m = __shfl_sync(kFull, my_m, k & 31);
       int e, j;
       M_ out;
-      const int dc = team_c2v<A, G>(g, s.C, s.L, i < nref ? m : -1, r, W, clip, e, j, out);
-      if (r < dc && j != nstar) s.P[e] = out;
-    }
-    __syncwarp();
-    uint32_t ck = 0, cidx = 0xffffffffu;
-    for (int i0 = 0; i0 < nref; i0 += tpw) {
-      const int i = i0 + team;
-      const int k = i < kstar ? i : i + 1;
-      const int m = __shfl_sync(kFull, my_m, k & 31);
-      if (i >= nref) continue;
-      const typename G::C cc = g.cn(m);
-      if (r >= cc.d) continue;
-      const int j = g.cvn(cc, r);
-      if (j == nstar) continue;
-      const L_ lt = vn_total<A, G>(g, s.lam, s.P, j);
-      const D_ d = ci_val(s, s.L[j], lt);
-      s.Lt[j] = lt;
-      s.D[j] = d;
-      am_update(ck, cidx, mkey(d), (uint32_t)j);
+      const int dc = team_c2v<A, G>(g, s.C, s.L, team < nref ? m : -1, r, W, clip, e, j, out);
+      const bool mine = r < dc && j != nstar;
+      if (mine) s.P[e] = out;
+      __syncwarp();
+      if (mine) {
+        const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
+        s.D[j] = d;
+        am_update(ck, cidx, mkey(d), (uint32_t)j);
+      }
+    } else {
+      for (int i0 = 0; i0 < nref; i0 += tpw) {
+        const int i = i0 + team;
+        const int k = i < kstar ? i : i + 1;
+        const int m = __shfl_sync(kFull, my_m, k & 31);
+        int e, j;
+        M_ out;
+        const int dc = team_c2v<A, G>(g, s.C, s.L, i < nref ? m : -1, r, W, clip, e, j, out);
+        if (r < dc && j != nstar) s.P[e] = out;
+      }
+      __syncwarp();
+      for (int i0 = 0; i0 < nref; i0 += tpw) {
+        const int i = i0 + team;
+        const int k = i < kstar ? i : i + 1;
+        const int m = __shfl_sync(kFull, my_m, k & 31);
+        if (i >= nref) continue;
+        const typename G::C cc = g.cn(m);
+        if (r >= cc.d) continue;
+        const int j = g.cvn(cc, r);
+        if (j == nstar) continue;
+        const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
+        s.D[j] = d;
+        am_update(ck, cidx, mkey(d), (uint32_t)j);
+      }
     }
     __syncwarp();
     if (kNeedR && lane < dv) refresh_rmax<A, G>(g, s, my_m);

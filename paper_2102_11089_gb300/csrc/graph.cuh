@@ -8,9 +8,9 @@
 //
 //  QCGraph   quasi-cyclic codes lifted from a protograph: every neighbour and
 //            edge id is computed from the protograph's block list (a few
-//            hundred entries in shared memory).  Check m = r Z + z has its
-//            k-th edge (block (r, c_k), shift s_k) at edge id
-//            rowbase[r] + z dc_r + k and variable c_k Z + (z + s_k) mod Z;
+//            hundred 16-byte entries in shared memory, one load per edge).
+//            Check m = r Z + z has its k-th edge (block (r, c_k), shift s_k) at
+//            edge id rowbase[r] + z dc_r + k and variable c_k Z + (z + s_k) mod Z;
 //            variable n = c Z + z meets check r Z + (z - s) mod Z of each block
 //            (r, c) of column c.
 //
@@ -55,13 +55,12 @@ struct TabGraph {
 };
 
 struct QCGraph {
-  const int32_t* rowbase;   // R+1 : first edge id of block row r
-  const int32_t* rowfirst;  // R+1 : first entry of row r in rowblk
-  const uint32_t* rowblk;   // nnz : (c << 16) | s, ascending c
-  const int32_t* colfirst;  // C+1 : first entry of column c in colblk
-  const uint32_t* colblk;   // nnz : (r << 24) | (k << 16) | s, ascending r
-  int R, Z;
-  uint32_t zmul, zshift;    // n / Z == __umulhi(n, zmul) >> zshift for n < R Z and C Z
+  const int4* rowinfo;  // R : {first edge id, first rowblk entry, d_c, r Z}
+  const int4* colinfo;  // C : {first colblk entry, d_v, c Z, 0}
+  const int4* colblk;   // nnz, by column then row: {s, r Z, rowbase[r] + k, d_c(r)}
+  const int2* rowblk;   // nnz, by row then column: {c Z, s}
+  int R, Z, E;
+  uint32_t zmul, zshift;  // n / Z == __umulhi(n, zmul) >> zshift for n < R Z and C Z
 
   __device__ __forceinline__ int divZ(int n) const { return (int)(__umulhi((uint32_t)n, zmul) >> zshift); }
 
@@ -72,39 +71,39 @@ struct QCGraph {
     int b, d, z, i0;
   };
   __device__ __forceinline__ V vn(int n) const {
-    const int c = divZ(n);
-    const int j0 = colfirst[c];
-    return {n - c * Z, j0, colfirst[c + 1] - j0};
+    const int4 ci = colinfo[divZ(n)];
+    return {n - ci.z, ci.x, ci.y};
   }
+  // k-th edge of variable c Z + z in block (r, c) with shift s: check r Z + (z - s) mod Z,
+  // edge id rowbase[r] + ((z - s) mod Z) d_c(r) + k
   __device__ __forceinline__ void vedge(const V& v, int k, int& e, int& m) const {
-    const uint32_t blk = colblk[v.j0 + k];
-    const int r = (int)(blk >> 24), kk = (int)((blk >> 16) & 255u), s = (int)(blk & 0xffffu);
-    int zz = v.z - s;
+    const int4 b = colblk[v.j0 + k];
+    int zz = v.z - b.x;
     zz += zz < 0 ? Z : 0;
-    m = r * Z + zz;
-    e = rowbase[r] + zz * (rowfirst[r + 1] - rowfirst[r]) + kk;
+    m = b.y + zz;
+    e = b.z + zz * b.w;
   }
   __device__ __forceinline__ C cn(int m) const {
-    const int r = divZ(m);
-    const int z = m - r * Z;
-    const int i0 = rowfirst[r], dc = rowfirst[r + 1] - i0;
-    return {rowbase[r] + z * dc, dc, z, i0};
+    const int4 ri = rowinfo[divZ(m)];
+    const int z = m - ri.w;
+    return {ri.x + z * ri.z, ri.z, z, ri.y};
   }
+  // k-th edge of check r Z + z, block (r, c_k) with shift s_k: variable c_k Z + (z + s_k) mod Z
   __device__ __forceinline__ int cvn(const C& c, int k) const {
-    const uint32_t blk = rowblk[c.i0 + k];
-    int zz = c.z + (int)(blk & 0xffffu);
+    const int2 b = rowblk[c.i0 + k];
+    int zz = c.z + b.y;
     zz -= zz >= Z ? Z : 0;
-    return (int)(blk >> 16) * Z + zz;
+    return b.x + zz;
   }
   __device__ __forceinline__ int ecn(int e) const {
-    int lo = 0, hi = R;  // rowbase[lo] <= e < rowbase[hi]
+    int lo = 0, hi = R;  // rowinfo[lo].x <= e < rowinfo[hi].x (rowinfo[R].x = E)
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
-      if (rowbase[mid] <= e) lo = mid;
+      if (rowinfo[mid].x <= e) lo = mid;
       else hi = mid;
     }
-    const int dc = rowfirst[lo + 1] - rowfirst[lo];
-    return lo * Z + (e - rowbase[lo]) / dc;
+    const int4 ri = rowinfo[lo];
+    return ri.w + (e - ri.x) / ri.z;
   }
   __device__ __forceinline__ int evn(int e) const {
     const int m = ecn(e);
@@ -157,13 +156,13 @@ struct GraphStage<QCGraph> {
     const int32_t* p = smem;
     g.R = d.qc_R;
     g.Z = d.qc_Z;
+    g.E = d.E;
     g.zmul = d.qc_zmul;
     g.zshift = d.qc_zshift;
-    g.rowbase = p; p += d.qc_R + 1;
-    g.rowfirst = p; p += d.qc_R + 1;
-    g.colfirst = p; p += d.qc_C + 1;
-    g.rowblk = (const uint32_t*)p; p += d.qc_nnz;
-    g.colblk = (const uint32_t*)p;
+    g.rowinfo = (const int4*)p; p += 4 * d.qc_R;
+    g.colinfo = (const int4*)p; p += 4 * d.qc_C;
+    g.colblk = (const int4*)p; p += 4 * d.qc_nnz;
+    g.rowblk = (const int2*)p;
     return g;
   }
 };

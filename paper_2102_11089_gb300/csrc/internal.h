@@ -21,8 +21,8 @@ constexpr int kMELMD = 5;
 
 // Device view of a code (canonical CSR edge order: by check, then variable).
 // `tab` = cn_ptr[M+1] | e_vn[E] | e_cn[E] | vn_ptr[N+1] | vn_e[E] (int32), always
-// present.  For codes lifted from a protograph `qc` holds
-// rowbase[R+1] | rowfirst[R+1] | colfirst[C+1] | rowblk[nnz] | colblk[nnz].
+// present.  For codes lifted from a protograph `qc` holds (see graph.cuh)
+// rowinfo[R] (int4) | colinfo[C] (int4) | colblk[nnz] (int4) | rowblk[nnz] (int2).
 struct GraphDesc {
   int32_t M, N, E;
   int32_t dv_max, dc_max, maxr;  // maxr = max_n sum_{m in M(n)} |N(m)|
@@ -62,6 +62,7 @@ struct DecodeArgs {
   int32_t smem_per_frame;
   int32_t graph_smem;    // bytes of staged graph tables at the start of shared memory
   int32_t team_w;        // lanes per check team: power of two >= max check degree
+  int32_t cta_threads;   // multi-edge CTA size (256 or 512)
   int16_t ci_table[256];  // INT6: round(32767 tanh(q * q_step / 2)), q = -127..127
 };
 
@@ -74,7 +75,7 @@ inline __host__ __device__ int graph_smem_bytes(const GraphDesc& d) {
 
 // Per-frame state layout of the single-edge (warp per frame) decoder.
 struct SELayout {
-  int C, P, lam, L, Lt, D, Rmax, Ridx, par, tab, total;
+  int C, P, lam, L, D, Rmax, Ridx, par, tab, total;
 };
 
 inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bool need_r) {
@@ -87,7 +88,6 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bo
   l.P = o; o = align16(o + E * msg);
   l.lam = o; o = align16(o + N * llr);
   l.L = o; o = align16(o + N * llr);
-  l.Lt = o; o = align16(o + N * llr);
   l.D = o; o = align16(o + N * dv);
   l.Rmax = o; o = align16(o + (need_r ? M * msg : 0));
   l.Ridx = o; o = align16(o + (need_r ? M * 4 : 0));
