@@ -100,8 +100,26 @@ typedef struct {
     uint64_t seed;          /* Algorithm 4 random fill (Philox4x32-10 key)         */
     uint64_t frame_offset;  /* global index of frame 0 of this batch (Philox ctr)  */
     int32_t form;           /* LDPC_FORM_*                                        */
-    int32_t reserved;       /* must be 0                                          */
+    int32_t tune;           /* launch-shape hints (0 = library defaults), set by the
+                               project's autotuner: bits 0-1 CTA size of CTA-per-frame
+                               kernels (1 = 256, 2 = 512 threads); bits 4-5 frame state
+                               of the queue form (1 = shared memory for codes whose
+                               state fits two CTAs per SM, 2 = fits one CTA per SM,
+                               3 = global memory only); other bits must be 0        */
 } ldpc_decode_params_t;
+
+/* One frame of the work queue of ldpc_decode_queue. */
+typedef struct {
+    int32_t code;          /* index into the call's array of codes               */
+    int32_t flags;         /* must be 0                                          */
+    int64_t llr_offset;    /* element offset of the frame's N LLRs in `llr`      */
+    int64_t out_offset;    /* element offset of the frame's N decisions in `hard` */
+    int64_t max_updates;   /* budget of this frame (committed C2V messages)      */
+    uint64_t frame_index;  /* global frame index (Algorithm 4's Philox counter)  */
+} ldpc_work_item_t;
+
+#define LDPC_QUEUE_STATIC 0     /* one CTA (single-edge: one warp) per item         */
+#define LDPC_QUEUE_PERSISTENT 1 /* resident CTAs take items until the queue is empty */
 
 /* Name of a status code (static string). */
 const char *ldpc_status_string(ldpc_status_t status);
@@ -176,6 +194,36 @@ ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batc
                           const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
                           uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);
 
+/* Decode a work queue of frames from up to 16 codes lifted from protographs
+ * (ldpc_code_build_qc), each frame with its own budget; the persistent form of
+ * the batched decoder.  In LDPC_QUEUE_PERSISTENT mode one launch of resident
+ * CTAs takes items through an atomic head counter, retires each frame at its
+ * syndrome stop (or budget) and takes the next, whatever its code; a code's
+ * protograph view is staged in shared memory when it changes.  In
+ * LDPC_QUEUE_STATIC mode the launch has one CTA per item (the plain per-batch
+ * form).  Schedules: LDPC_LMD_CIRBP, LDPC_ME_CIRBP, LDPC_ME_LMD_CIRBP.
+ * codes   : host array of n_codes handles (1..16), each with a protograph view
+ * items   : device ldpc_work_item_t[n_items]
+ * llr     : device base of the LLR rows (float, or int8 for INT6)
+ * hard    : device base of the decision rows, or NULL
+ * updates : device int64[n_items] or NULL    converged : device uint8[n_items] or NULL
+ * params  : as ldpc_decode (max_updates unused: each item carries its budget;
+ *           form ignored; tune bits 0-1 and 4-5 apply)
+ * The call is asynchronous and allocates only stream-ordered memory (the head
+ * counter and global state slots, cudaMallocAsync / cudaFreeAsync on `stream`);
+ * once every code has been used on the device (first call), it can be
+ * recorded into a CUDA graph.
+ * Offsets are not checked against the buffers (the caller sizes them); an
+ * item whose code index is outside 0..n_codes-1 is not decoded: its
+ * converged flag is LDPC_FRAME_BAD_INPUT, its updates 0, and the next
+ * ldpc_sync returns LDPC_ERR_INVALID_ARG.
+ * Errors: INVALID_ARG, UNSUPPORTED (a code without protograph view, schedule,
+ * degrees, more than 2^31 - 2^20 items), CUDA, NOMEM. */
+ldpc_status_t ldpc_decode_queue(const ldpc_code_t *const *codes, int32_t n_codes, const ldpc_work_item_t *items,
+                                int64_t n_items, const void *llr, const ldpc_decode_params_t *params,
+                                uint8_t *hard, int64_t *updates, uint8_t *converged, int32_t mode,
+                                void *cuda_stream);
+
 /* Decode like ldpc_decode, but without allocating any memory.  The paper has
  * no counterpart: this is a service of the library, not a step of the method.
  *
@@ -210,8 +258,9 @@ ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t *code, const void *llr, int6
 
 /* Wait for `cuda_stream` and return the device status accumulated by decode
  * calls on the current device since the previous ldpc_sync (the status word
- * is then cleared): LDPC_OK, LDPC_ERR_NONFINITE_LLR, LDPC_ERR_TIMEOUT or
- * LDPC_ERR_CUDA for a failed stream. */
+ * is then cleared): LDPC_OK, LDPC_ERR_NONFINITE_LLR, LDPC_ERR_TIMEOUT,
+ * LDPC_ERR_INVALID_ARG (a queue item with a bad code index) or LDPC_ERR_CUDA
+ * for a failed stream. */
 ldpc_status_t ldpc_sync(void *cuda_stream);
 
 #ifdef __cplusplus

@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 __all__ = [
-    "LdpcError", "Code", "DecodeParams", "decode", "decode_noalloc", "awgn_llr", "sync", "library_path",
+    "LdpcError", "Code", "DecodeParams", "decode", "decode_noalloc", "decode_queue", "make_items", "awgn_llr",
+    "sync", "library_path", "QUEUE_STATIC", "QUEUE_PERSISTENT",
     "SCHEDULES", "FLOODING", "RBP", "CIRBP", "LMD_CIRBP", "ME_CIRBP", "ME_LMD_CIRBP",
     "FP32_SUMPRODUCT", "INT6_MINSUM", "FORM_AUTO", "FORM_SMEM", "FORM_GLOBAL",
 ]
@@ -50,7 +51,7 @@ class DecodeParams(ctypes.Structure):
         ("max_updates", ctypes.c_int64), ("check_interval", ctypes.c_int64),
         ("llr_clip", ctypes.c_float), ("q_step", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("frame_offset", ctypes.c_uint64),
-        ("form", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("form", ctypes.c_int32), ("tune", ctypes.c_int32),
     ]
 
 
@@ -86,6 +87,7 @@ def _load():
             ("ldpc_awgn_llr", [P, P, I64, U64, U64, P, P, ctypes.c_float, P]),
             ("ldpc_decode", [P, P, I64, P, P, P, P, P, P, P]),
             ("ldpc_decode_noalloc", [P, P, I64, P, P, P, P, P, P, P]),
+            ("ldpc_decode_queue", [P, I32, P, I64, P, P, P, P, P, I32, P]),
             ("ldpc_sync", [P]),
         ]:
             f = getattr(h, name)
@@ -176,7 +178,7 @@ def _stream_ptr(stream):
 
 def make_params(schedule="lmd-cirbp", arith="fp32", *, gamma=0.1, n_p=16, n_g=16,
                 max_updates=0, check_interval=1, llr_clip=25.0, q_step=0.5, seed=0,
-                frame_offset=0, form=FORM_AUTO) -> DecodeParams:
+                frame_offset=0, form=FORM_AUTO, tune=0) -> DecodeParams:
     p = DecodeParams()
     _check(_load().ldpc_default_params(ctypes.byref(p)))
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -184,6 +186,7 @@ def make_params(schedule="lmd-cirbp", arith="fp32", *, gamma=0.1, n_p=16, n_g=16
     p.gamma, p.n_p, p.n_g = gamma, n_p, n_g
     p.max_updates, p.check_interval = max_updates, check_interval
     p.llr_clip, p.q_step, p.seed, p.frame_offset, p.form = llr_clip, q_step, seed, frame_offset, form
+    p.tune = tune
     return p
 
 
@@ -236,6 +239,34 @@ def decode_noalloc(code: Code, llr, params: DecodeParams, out: dict, stream=None
                                        ptr("converged"), ptr("trace"), ptr("llr"),
                                        _stream_ptr(stream)))
     return out
+
+
+QUEUE_STATIC, QUEUE_PERSISTENT = 0, 1
+WORK_ITEM_DTYPE = np.dtype([("code", "<i4"), ("flags", "<i4"), ("llr_offset", "<i8"),
+                            ("out_offset", "<i8"), ("max_updates", "<i8"), ("frame_index", "<u8")])
+
+
+def make_items(code, llr_offset, out_offset, max_updates, frame_index, device="cuda"):
+    """Device array of ldpc_work_item_t (40 bytes each) from per-item columns."""
+    import torch
+    n = len(code)
+    a = np.zeros(n, dtype=WORK_ITEM_DTYPE)
+    a["code"], a["llr_offset"], a["out_offset"] = code, llr_offset, out_offset
+    a["max_updates"], a["frame_index"] = max_updates, frame_index
+    return torch.from_numpy(a.view(np.uint8).copy()).to(device)
+
+
+def decode_queue(codes, items, n_items: int, llr, params: DecodeParams, *, hard=None, updates=None,
+                 converged=None, mode=QUEUE_PERSISTENT, stream=None):
+    """ldpc_decode_queue: frames of several lifted codes, each with its own
+    budget, from a device work queue (see make_items)."""
+    arr = (ctypes.c_void_p * len(codes))(*[c._h for c in codes])
+
+    def ptr(t):
+        return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+    _check(_load().ldpc_decode_queue(arr, len(codes), ptr(items), n_items, ptr(llr), ctypes.byref(params),
+                                     ptr(hard), ptr(updates), ptr(converged), mode, _stream_ptr(stream)))
 
 
 def awgn_llr(code: Code, ebn0_db, seed: int, frame_offset: int = 0, *, quantize=False,

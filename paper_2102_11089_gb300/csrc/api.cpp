@@ -494,8 +494,8 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 1024))
     return fail(LDPC_ERR_INVALID_ARG, "n_p > 0 and 0 < n_g <= 1024 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || p->reserved != 0)
-    return fail(LDPC_ERR_INVALID_ARG, "bad form / reserved");
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
+    return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
 
@@ -534,7 +534,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   // multi-edge CTA size: FP32 frames run two CTAs per SM (shared memory), where 512
   // threads hide more latency; 6-bit frames run four 256-thread CTAs per SM
   a.cta_threads = p->arith == LDPC_INT6_MINSUM ? 256 : 512;
-  if (const char* t = std::getenv("LDPC_ME_THREADS")) a.cta_threads = std::atoi(t) == 512 ? 512 : 256;
+  if ((p->tune & 3) != 0) a.cta_threads = (p->tune & 3) == 2 ? 512 : 256;
   if (p->arith == LDPC_INT6_MINSUM)
     for (int q = -127; q <= 127; ++q)
       a.ci_table[q + 127] = (int16_t)std::round(32767.0 * std::tanh(q * (double)p->q_step / 2.0));
@@ -604,6 +604,119 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   return LDPC_OK;
 }
 
+ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes, const ldpc_work_item_t* items,
+                                int64_t n_items, const void* llr, const ldpc_decode_params_t* p, uint8_t* hard,
+                                int64_t* updates, uint8_t* converged, int32_t mode, void* cuda_stream) {
+  static_assert(sizeof(ldpc_work_item_t) == sizeof(ldpc::WorkItem), "work item layout");
+  if (!codes || !p || n_codes < 1 || n_codes > ldpc::kMaxQueueCodes)
+    return fail(LDPC_ERR_INVALID_ARG, "1..16 codes and params are required");
+  if (n_items < 0 || (mode != LDPC_QUEUE_STATIC && mode != LDPC_QUEUE_PERSISTENT))
+    return fail(LDPC_ERR_INVALID_ARG, "bad item count or mode");
+  // the head counter is 32-bit and each CTA takes one item past the end
+  if (n_items > ((int64_t)1 << 31) - ((int64_t)1 << 20)) return fail(LDPC_ERR_UNSUPPORTED, "more than 2^31 - 2^20 items");
+  if (p->schedule != LDPC_LMD_CIRBP && p->schedule != LDPC_ME_CIRBP && p->schedule != LDPC_ME_LMD_CIRBP)
+    return fail(LDPC_ERR_UNSUPPORTED, "queue form: LMD-CIRBP, ME-CIRBP or ME-LMD-CIRBP");
+  if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
+    return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
+  if (p->check_interval < 0 || !(p->gamma >= 0.0 && p->gamma <= 1.0) || !(p->llr_clip > 0.0f) ||
+      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
+    return fail(LDPC_ERR_INVALID_ARG, "bad parameters");
+  const bool me = p->schedule != LDPC_LMD_CIRBP;
+  if (me && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 255)) return fail(LDPC_ERR_INVALID_ARG, "n_p, n_g");
+  if (n_items == 0) return LDPC_OK;
+  if (!items || !llr) return fail(LDPC_ERR_INVALID_ARG, "items and llr are required");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint32_t* status;
+  ldpc_status_t st = device_status_word(dev, &status);
+  if (st) return st;
+  const int arith = p->arith == LDPC_INT6_MINSUM ? ldpc::kINT6 : ldpc::kFP32;
+  ldpc::QueueArgs q;
+  std::memset(&q, 0, sizeof(q));
+  size_t graph_bytes = 0, small_bytes = 0, big_max = 0;
+  std::vector<size_t> bigs;
+  for (int i = 0; i < n_codes; ++i) {
+    if (!codes[i]) return fail(LDPC_ERR_INVALID_ARG, "NULL code");
+    const ldpc::GraphDesc* g;
+    st = ensure_device(const_cast<ldpc_code_t*>(codes[i]), &g, nullptr);
+    if (st) return st;
+    if (!g->is_qc) return fail(LDPC_ERR_UNSUPPORTED, "queue form needs codes built by ldpc_code_build_qc");
+    if (g->dc_max > 32 || g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "degree > 32");
+    q.codes[i] = *g;
+    graph_bytes = std::max(graph_bytes, (size_t)ldpc::graph_smem_bytes(*g));
+    const size_t big = me ? ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g)
+                          : ldpc::se_smem_per_frame(arith, p->schedule, *g);
+    bigs.push_back(big);
+    big_max = std::max(big_max, big);
+    if (me) small_bytes = std::max(small_bytes, ldpc::me_smem_per_cta(*g, p->n_p, p->n_g));
+  }
+  const int optin = max_optin_smem();
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t fixed = graph_bytes + small_bytes + (me ? 1024 : 0);
+  if ((int64_t)fixed > optin) return fail(LDPC_ERR_UNSUPPORTED, "working set exceeds shared memory");
+  // frame state in shared memory for codes up to a size: two CTAs per SM by
+  // default (or one, or none, by tune bits 4-5); larger codes use global slots
+  const int placement = (p->tune >> 4) & 3;
+  const size_t budget = placement == 3 ? 0 : (placement == 2 ? (size_t)optin - fixed : (size_t)optin / 2 - fixed);
+  size_t sstate = 0;
+  for (size_t b : bigs)
+    if (b <= budget) sstate = std::max(sstate, b);
+  const int threads = me ? ((p->tune & 3) == 1 ? 256 : ((p->tune & 3) == 2 ? 512 : (arith == ldpc::kINT6 ? 256 : 512))) : 32;
+  const size_t smem = fixed + sstate;
+  int grid;
+  if (mode == LDPC_QUEUE_PERSISTENT) {
+    int per_sm = me ? std::max(1, (int)std::min<size_t>(2048 / threads, (size_t)228 * 1024 / (smem + 1024)))
+                    : std::max(1, (int)std::min<size_t>(32, (size_t)228 * 1024 / (smem + 1024)));
+    grid = (int)std::min<int64_t>(n_items, (int64_t)sms * per_sm);
+  } else {
+    if (n_items > 0x7fffffff) return fail(LDPC_ERR_UNSUPPORTED, "too many items for one launch");
+    grid = (int)n_items;
+  }
+  const size_t stride = ((big_max + 255) / 256) * 256;
+  const bool need_global = sstate < big_max;
+  const size_t bytes = 256 + (need_global ? (size_t)grid * stride : 0);
+  void* scratch = nullptr;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
+  if (e != cudaSuccess) return fail(LDPC_ERR_NOMEM, std::string("cudaMallocAsync(queue): ") + cudaGetErrorString(e));
+  e = cudaMemsetAsync(scratch, 0, 256, s);
+  ldpc::DecodeArgs& a = q.a;
+  a.llr = llr;
+  a.batch = n_items;
+  a.hard = hard;
+  a.updates = updates;
+  a.converged = converged;
+  a.check_interval = p->check_interval;
+  a.gamma_f = (float)p->gamma;
+  a.gamma_i = (int32_t)std::round(p->gamma * 65534.0);
+  a.llr_clip = p->llr_clip;
+  a.n_p = p->n_p;
+  a.n_g = p->n_g;
+  a.seed = p->seed;
+  a.status = status;
+  a.gstate = need_global ? (unsigned char*)scratch + 256 : nullptr;
+  a.gstate_stride = (int64_t)stride;
+  if (arith == ldpc::kINT6)
+    for (int qq = -127; qq <= 127; ++qq)
+      a.ci_table[qq + 127] = (int16_t)std::round(32767.0 * std::tanh(qq * (double)p->q_step / 2.0));
+  q.n_codes = n_codes;
+  q.items = (const ldpc::WorkItem*)items;
+  q.n_items = n_items;
+  q.head = (unsigned int*)scratch;
+  q.persistent = mode == LDPC_QUEUE_PERSISTENT;
+  q.graph_bytes = (int32_t)graph_bytes;
+  q.small_bytes = (int32_t)small_bytes;
+  q.smem_state_bytes = (int32_t)sstate;
+  if (e == cudaSuccess)
+    e = me ? ldpc::launch_me_queue(q, arith, p->schedule, threads, grid, smem, s)
+           : ldpc::launch_se_queue(q, arith, grid, smem, s);
+  const cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "queue launch");
+  return LDPC_OK;
+}
+
 ldpc_status_t ldpc_sync(void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -620,6 +733,7 @@ ldpc_status_t ldpc_sync(void* cuda_stream) {
     if (e != cudaSuccess) return cuda_fail(e, "clear status");
   }
   if (v & 2u) return fail(LDPC_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (v & 4u) return fail(LDPC_ERR_INVALID_ARG, "a queue item named a code outside its call's code list");
   if (v & 1u) return fail(LDPC_ERR_NONFINITE_LLR, "a decode saw a non-finite or out-of-range LLR");
   return LDPC_OK;
 }

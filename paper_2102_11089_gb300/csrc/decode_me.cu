@@ -291,18 +291,18 @@ __device__ void compact_selection(int N, const MEState<A>& s, int np) {
   __syncthreads();
 }
 
-// Decode frame b: big arrays at `big`, per-CTA working set at `small`.
+// Decode one frame of code `gd`: big arrays at `big`, per-CTA working set at `small`.
 template <int A, int SCHED, class G>
-__device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_t b, unsigned char* big,
-                                         unsigned char* small, const int16_t* tab_int) {
+__device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& gd, const G& g, const FrameIO& io,
+                                         unsigned char* big, unsigned char* small, const int16_t* tab_int) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int N = a.g.N, E = a.g.E, M = a.g.M;
+  const int N = gd.N, E = gd.E, M = gd.M;
   const int np = a.n_p, ng = a.n_g;
   const MEBig lb = me_big(A, M, N, E);
-  const MESmall ls = me_small(N, np, a.g.dv_max, ng);
+  const MESmall ls = me_small(N, np, gd.dv_max, ng);
   MEState<A> s;
   s.C = (M_*)(big + lb.C);
   s.P = (M_*)(big + lb.P);
@@ -325,18 +325,18 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   s.tab = tab_int;
   MEMisc* ms = s.misc;
   const float clip = a.llr_clip;
-  const uint64_t frame = a.frame_offset + (uint64_t)b;
-  const int W = a.team_w, tpw = 32 / W, team = lane / W, r = lane % W;
+  const uint64_t frame = io.frame;
+  const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
 
   int bad = 0;
   for (int n = tid; n < N; n += nt) {
     L_ v;
     if (A == kFP32) {
-      const float x = ((const float*)a.llr)[b * N + n];
+      const float x = ((const float*)io.llr)[n];
       bad |= !isfinite(x);
       v = (L_)x;
     } else {
-      const int x = ((const int8_t*)a.llr)[b * N + n];
+      const int x = ((const int8_t*)io.llr)[n];
       bad |= (x < -31 || x > 31);
       v = (L_)x;
     }
@@ -357,12 +357,12 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   }
   if (__syncthreads_or(bad)) {
     for (int n = tid; n < N; n += nt) {
-      if (a.hard) a.hard[b * N + n] = 0;
-      if (a.llr_out) a.llr_out[b * N + n] = (float)s.lam[n];
+      if (io.hard) io.hard[n] = 0;
+      if (io.llr_out) io.llr_out[n] = (float)s.lam[n];
     }
     if (tid == 0) {
-      if (a.updates) a.updates[b] = 0;
-      if (a.converged) a.converged[b] = 2;
+      if (io.updates) *io.updates = 0;
+      if (io.converged) *io.converged = 2;
       atomicOr(a.status, 1u);
     }
     return;
@@ -395,14 +395,14 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   int64_t count = 0;
   uint32_t step = 0;
   bool stop = a.check_interval > 0 && ms->unsat == 0;
-  if (!stop && a.max_updates > 0) {  // Alg. 5 line 4 / Alg. 6 line 4
+  if (!stop && io.max_updates > 0) {  // Alg. 5 line 4 / Alg. 6 line 4
     alg4<A>(s, N, np, ng, 0, step, frame, a.seed);
     compact_selection<A>(N, s, np);
   }
-  while (!stop && count < a.max_updates) {
+  while (!stop && count < io.max_updates) {
     int nsel = ms->nsel;
     if (nsel <= 0) break;  // nothing selectable: the step would not advance
-    if ((int64_t)nsel > a.max_updates - count) nsel = (int)(a.max_updates - count);
+    if ((int64_t)nsel > io.max_updates - count) nsel = (int)(io.max_updates - count);
     // -- for each selected p: m*_p = argmax_i R_{i->p} on the pre-step state (the
     //    edges of p are disjoint from every other p's), commit L^C <- L~^C, L_p,
     //    syndrome, trace, the checks i in M(p)\m*_p whose inputs changed
@@ -441,7 +441,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
           s.cnl[pos] = make_int2(m, k);
         }
       }
-      if (a.trace) a.trace[b * a.max_updates + count + k] = es;
+      if (io.trace) io.trace[count + k] = es;
     }
     __syncthreads();
     const int ncn = ms->ncn;
@@ -491,7 +491,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
     if (a.check_interval > 0 && (count / a.check_interval) > ((count - nsel) / a.check_interval) &&
         ms->unsat == 0)
       break;
-    if (count >= a.max_updates) break;
+    if (count >= io.max_updates) break;
     if (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
       alg4<A>(s, N, np, ng, 0, step, frame, a.seed);  // Alg. 5 line 4
       compact_selection<A>(N, s, np);
@@ -527,12 +527,12 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const G& g, int64_
   }
 
   for (int n = tid; n < N; n += nt) {
-    if (a.hard) a.hard[b * N + n] = (uint8_t)(s.L[n] < (L_)0);
-    if (a.llr_out) a.llr_out[b * N + n] = (float)s.L[n];
+    if (io.hard) io.hard[n] = (uint8_t)(s.L[n] < (L_)0);
+    if (io.llr_out) io.llr_out[n] = (float)s.L[n];
   }
   if (tid == 0) {
-    if (a.updates) a.updates[b] = count;
-    if (a.converged) a.converged[b] = ms->unsat == 0 ? 1 : 0;
+    if (io.updates) *io.updates = count;
+    if (io.converged) *io.converged = ms->unsat == 0 ? 1 : 0;
   }
   __syncthreads();
 }
@@ -554,7 +554,8 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_k
   if (A == kINT6)
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   unsigned char* big = smem_raw + a.graph_smem;
-  me_frame<A, SCHED, G>(a, g, blockIdx.x, big, big + a.smem_per_frame, tab_int);
+  me_frame<A, SCHED, G>(a, a.g, g, batch_io(a, blockIdx.x, A == kINT6 ? 1 : 4), big, big + a.smem_per_frame,
+                        tab_int);
 }
 
 // Global-memory form: CTA c owns state slot c of a.gstate and decodes frames
@@ -568,7 +569,70 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_k
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   unsigned char* big = (unsigned char*)a.gstate + (int64_t)blockIdx.x * a.gstate_stride;
   for (int64_t b = blockIdx.x; b < a.batch; b += gridDim.x)
-    me_frame<A, SCHED, G>(a, g, b, big, smem_raw + a.graph_smem, tab_int);
+    me_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), big, smem_raw + a.graph_smem, tab_int);
+}
+
+// Queue form: CTAs take work items (frames of any of up to 16 lifted codes, each
+// with its own budget) until the queue is empty; a code's protograph view is
+// staged when it changes; frame state sits in shared memory when it fits the
+// CTA's reservation, else in the CTA's global slot.
+template <int A, int SCHED, int TPB>
+__global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_queue_kernel(const QueueArgs q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int16_t tab_int[256];
+  __shared__ GraphDesc s_gd;
+  __shared__ long long s_item;
+  const int tid = threadIdx.x;
+  if (A == kINT6)
+    for (int i = tid; i < 256; i += blockDim.x) tab_int[i] = q.a.ci_table[i];
+  unsigned char* small = smem_raw + q.graph_bytes;
+  unsigned char* sstate = small + q.small_bytes;
+  unsigned char* gslot = (unsigned char*)q.a.gstate + (int64_t)blockIdx.x * q.a.gstate_stride;
+  int cur = -1;
+  QCGraph g{};
+  for (int64_t round = 0;; ++round) {
+    __syncthreads();  // every thread has read the previous item index
+    if (tid == 0) s_item = q.persistent ? (long long)atomicAdd(q.head, 1u) : (round == 0 ? (long long)blockIdx.x : q.n_items);
+    __syncthreads();
+    const int64_t idx = s_item;
+    if (idx >= q.n_items) break;
+    const WorkItem it = q.items[idx];
+    if (it.code < 0 || it.code >= q.n_codes) {  // not a code of this call: flag the item
+      if (tid == 0) {
+        if (q.a.updates) q.a.updates[idx] = 0;
+        if (q.a.converged) q.a.converged[idx] = 2;
+        atomicOr(q.a.status, 4u);
+      }
+      continue;
+    }
+    if (it.code != cur) {
+      if (tid == 0) s_gd = q.codes[it.code];
+      __syncthreads();
+      g = GraphStage<QCGraph>::make(s_gd, (int32_t*)smem_raw);
+      cur = it.code;
+    }
+    const int elem = A == kINT6 ? 1 : 4;
+    FrameIO io;
+    io.llr = (const unsigned char*)q.a.llr + it.llr_offset * elem;
+    io.hard = q.a.hard ? q.a.hard + it.out_offset : nullptr;
+    io.llr_out = nullptr;
+    io.updates = q.a.updates ? q.a.updates + idx : nullptr;
+    io.converged = q.a.converged ? q.a.converged + idx : nullptr;
+    io.trace = nullptr;
+    io.max_updates = it.max_updates;
+    io.frame = it.frame_index;
+    const int big = me_big(A, s_gd.M, s_gd.N, s_gd.E).total;
+    me_frame<A, SCHED, QCGraph>(q.a, s_gd, g, io, big <= q.smem_state_bytes ? sstate : gslot, small, tab_int);
+  }
+}
+
+template <int A, int S, int TPB>
+cudaError_t launch_me_queue_tpb(const QueueArgs& q, int grid, size_t smem, cudaStream_t st) {
+  auto k = me_queue_kernel<A, S, TPB>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k<<<(unsigned)grid, TPB, smem, st>>>(q);
+  return cudaGetLastError();
 }
 
 template <int A, int S, class G, int TPB>
@@ -602,6 +666,18 @@ cudaError_t launch_me_sched(const DecodeArgs& a, int sched, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int threads, int grid, size_t smem,
+                            cudaStream_t s) {
+  if (q.n_items == 0) return cudaSuccess;
+  const bool lmd = sched == kMELMD, big = threads == 512;
+  if (arith == kFP32) {
+    if (lmd) return big ? launch_me_queue_tpb<kFP32, kMELMD, 512>(q, grid, smem, s) : launch_me_queue_tpb<kFP32, kMELMD, 256>(q, grid, smem, s);
+    return big ? launch_me_queue_tpb<kFP32, kMECIRBP, 512>(q, grid, smem, s) : launch_me_queue_tpb<kFP32, kMECIRBP, 256>(q, grid, smem, s);
+  }
+  if (lmd) return big ? launch_me_queue_tpb<kINT6, kMELMD, 512>(q, grid, smem, s) : launch_me_queue_tpb<kINT6, kMELMD, 256>(q, grid, smem, s);
+  return big ? launch_me_queue_tpb<kINT6, kMECIRBP, 512>(q, grid, smem, s) : launch_me_queue_tpb<kINT6, kMECIRBP, 256>(q, grid, smem, s);
+}
 
 size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g) {
   (void)sched;

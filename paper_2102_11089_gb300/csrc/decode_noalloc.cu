@@ -82,8 +82,8 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 255))
     return fail(LDPC_ERR_INVALID_ARG, "n_p > 0 and 0 < n_g <= 255 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || p->reserved != 0)
-    return fail(LDPC_ERR_INVALID_ARG, "bad form / reserved");
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
+    return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
   if (v.dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
@@ -158,6 +158,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   a.team_w = 1;
   while (a.team_w < g.dc_max) a.team_w <<= 1;
   a.cta_threads = p->arith == LDPC_INT6_MINSUM ? 256 : 512;
+  if ((p->tune & 3) != 0) a.cta_threads = (p->tune & 3) == 2 ? 512 : 256;
   const int arith = p->arith == LDPC_INT6_MINSUM ? ldpc::kINT6 : ldpc::kFP32;
   if (arith == ldpc::kINT6)
     for (int q = -127; q <= 127; ++q)

@@ -103,15 +103,16 @@ __device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, in
   s.Ridx[m] = (int32_t)bi;
 }
 
-// Decode frame b with its state at `base` (shared or global memory).
+// Decode one frame of code `gd` with its state at `base` (shared or global memory).
 template <int A, int SCHED, class G>
-__device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_t b, unsigned char* base) {
+__device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& gd, const G& g, const FrameIO& io,
+                                         unsigned char* base) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   constexpr bool kNeedR = SCHED != kLMD;
   const int lane = threadIdx.x & 31;
-  const int N = a.g.N, E = a.g.E, M = a.g.M;
+  const int N = gd.N, E = gd.E, M = gd.M;
   const SELayout ly = se_layout(A, M, N, E, kNeedR);
   SEState<A> s;
   s.C = (M_*)(base + ly.C);
@@ -124,7 +125,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
   s.par = (uint32_t*)(base + ly.par);
   s.tab = (int16_t*)(base + ly.tab);
   const float clip = a.llr_clip;
-  const int W = a.team_w, tpw = 32 / W, team = lane / W, r = lane % W;
+  const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
 
   if (A == kINT6)
     for (int i = lane; i < 256; i += 32) s.tab[i] = a.ci_table[i];
@@ -135,11 +136,11 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
   for (int n = lane; n < N; n += 32) {
     L_ v;
     if (A == kFP32) {
-      const float x = ((const float*)a.llr)[b * N + n];
+      const float x = ((const float*)io.llr)[n];
       bad |= !isfinite(x);
       v = (L_)x;
     } else {
-      const int x = ((const int8_t*)a.llr)[b * N + n];
+      const int x = ((const int8_t*)io.llr)[n];
       bad |= (x < -31 || x > 31);
       v = (L_)x;
     }
@@ -149,12 +150,12 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
   for (int e = lane; e < E; e += 32) s.C[e] = (M_)0;
   if (__any_sync(kFull, bad)) {
     for (int n = lane; n < N; n += 32) {
-      if (a.hard) a.hard[b * N + n] = 0;
-      if (a.llr_out) a.llr_out[b * N + n] = (float)s.lam[n];
+      if (io.hard) io.hard[n] = 0;
+      if (io.llr_out) io.llr_out[n] = (float)s.lam[n];
     }
     if (lane == 0) {
-      if (a.updates) a.updates[b] = 0;
-      if (a.converged) a.converged[b] = 2;
+      if (io.updates) *io.updates = 0;
+      if (io.converged) *io.converged = 2;
       atomicOr(a.status, 1u);
     }
     return;
@@ -196,7 +197,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
     uint32_t k;
     nstar = global_argmax_D<A>(N, s, k);  // Alg. 3 line 4
   }
-  while (!stop && count < a.max_updates) {
+  while (!stop && count < io.max_updates) {
     // -- selection
     int eglob = -1;  // RBP / CIRBP fallback: the global residual argmax fixes e*
     if (SCHED == kRBP) {
@@ -261,7 +262,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
       }
       unsat += __reduce_add_sync(kFull, delta);
     }
-    if (lane == 0 && a.trace) a.trace[b * a.max_updates + count] = estar;
+    if (lane == 0 && io.trace) io.trace[count] = estar;
     __syncwarp();
 
     // -- refresh (Alg. 1 lines 10-13): team i handles the i-th check of M(n*)\m*:
@@ -335,12 +336,12 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const G& g, int64_
 
   // ---- outputs
   for (int n = lane; n < N; n += 32) {
-    if (a.hard) a.hard[b * N + n] = (uint8_t)(s.L[n] < (L_)0);
-    if (a.llr_out) a.llr_out[b * N + n] = (float)s.L[n];
+    if (io.hard) io.hard[n] = (uint8_t)(s.L[n] < (L_)0);
+    if (io.llr_out) io.llr_out[n] = (float)s.L[n];
   }
   if (lane == 0) {
-    if (a.updates) a.updates[b] = count;
-    if (a.converged) a.converged[b] = unsat == 0 ? 1 : 0;
+    if (io.updates) *io.updates = count;
+    if (io.converged) *io.converged = unsat == 0 ? 1 : 0;
   }
   __syncwarp();
 }
@@ -353,7 +354,8 @@ __global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
   const int warp = threadIdx.x >> 5;
   const int64_t b = (int64_t)blockIdx.x * a.frames_per_cta + warp;
   if (b >= a.batch) return;
-  se_frame<A, SCHED, G>(a, g, b, smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame);
+  se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4),
+                        smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame);
 }
 
 // Global-memory form (frame state larger than shared memory): every warp owns
@@ -366,7 +368,62 @@ __global__ void __launch_bounds__(512) se_decode_kernel_gs(const DecodeArgs a) {
   const int64_t slot = (int64_t)blockIdx.x * a.frames_per_cta + warp;
   const int64_t slots = (int64_t)gridDim.x * a.frames_per_cta;
   unsigned char* base = (unsigned char*)a.gstate + slot * a.gstate_stride;
-  for (int64_t b = slot; b < a.batch; b += slots) se_frame<A, SCHED, G>(a, g, b, base);
+  for (int64_t b = slot; b < a.batch; b += slots) se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), base);
+}
+
+// Queue form of the single-edge schedules: one warp per CTA takes work items
+// until the queue is empty (see the multi-edge queue kernel).
+template <int A, int SCHED>
+__global__ void __launch_bounds__(32) se_queue_kernel(const QueueArgs q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ GraphDesc s_gd;
+  const int lane = threadIdx.x & 31;
+  unsigned char* sstate = smem_raw + q.graph_bytes;
+  unsigned char* gslot = (unsigned char*)q.a.gstate + (int64_t)blockIdx.x * q.a.gstate_stride;
+  int cur = -1;
+  QCGraph g{};
+  for (int64_t round = 0;; ++round) {
+    long long idx = 0;
+    if (lane == 0) idx = q.persistent ? (long long)atomicAdd(q.head, 1u) : (round == 0 ? (long long)blockIdx.x : q.n_items);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx >= q.n_items) break;
+    const WorkItem it = q.items[idx];
+    if (it.code < 0 || it.code >= q.n_codes) {  // not a code of this call: flag the item
+      if (lane == 0) {
+        if (q.a.updates) q.a.updates[idx] = 0;
+        if (q.a.converged) q.a.converged[idx] = 2;
+        atomicOr(q.a.status, 4u);
+      }
+      continue;
+    }
+    if (it.code != cur) {
+      if (lane == 0) s_gd = q.codes[it.code];
+      __syncwarp();
+      g = GraphStage<QCGraph>::make(s_gd, (int32_t*)smem_raw);
+      cur = it.code;
+    }
+    const int elem = A == kINT6 ? 1 : 4;
+    FrameIO io;
+    io.llr = (const unsigned char*)q.a.llr + it.llr_offset * elem;
+    io.hard = q.a.hard ? q.a.hard + it.out_offset : nullptr;
+    io.llr_out = nullptr;
+    io.updates = q.a.updates ? q.a.updates + idx : nullptr;
+    io.converged = q.a.converged ? q.a.converged + idx : nullptr;
+    io.trace = nullptr;
+    io.max_updates = it.max_updates;
+    io.frame = it.frame_index;
+    const int bytes = se_layout(A, s_gd.M, s_gd.N, s_gd.E, SCHED != kLMD).total;
+    se_frame<A, SCHED, QCGraph>(q.a, s_gd, g, io, bytes <= q.smem_state_bytes ? sstate : gslot);
+  }
+}
+
+template <int A, int S>
+cudaError_t launch_se_queue_t(const QueueArgs& q, int grid, size_t smem, cudaStream_t st) {
+  auto k = se_queue_kernel<A, S>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k<<<(unsigned)grid, 32, smem, st>>>(q);
+  return cudaGetLastError();
 }
 
 template <int A, int S, class G>
@@ -396,6 +453,11 @@ cudaError_t launch_sched(const DecodeArgs& a, int sched, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem, cudaStream_t s) {
+  if (q.n_items == 0) return cudaSuccess;
+  return arith == kFP32 ? launch_se_queue_t<kFP32, kLMD>(q, grid, smem, s) : launch_se_queue_t<kINT6, kLMD>(q, grid, smem, s);
+}
 
 size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g) {
   return (size_t)se_layout(arith, g.M, g.N, g.E, sched != kLMD).total;

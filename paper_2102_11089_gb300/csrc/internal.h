@@ -66,7 +66,41 @@ struct DecodeArgs {
   int16_t ci_table[256];  // INT6: round(32767 tanh(q * q_step / 2)), q = -127..127
 };
 
+// Per-frame inputs and outputs of one decode (built from DecodeArgs for frame b
+// of a batch, or from a work item of the queue form).
+struct FrameIO {
+  const void* llr;     // this frame's N channel LLRs (float or int8)
+  uint8_t* hard;       // N decisions, or null
+  float* llr_out;      // N final LLRs, or null
+  int64_t* updates;    // update count, or null
+  uint8_t* converged;  // flags, or null
+  int32_t* trace;      // max_updates edge ids, or null
+  int64_t max_updates;
+  uint64_t frame;  // global frame index (Algorithm 4's Philox counter)
+};
+
 inline __host__ __device__ int align16(int x) { return (x + 15) & ~15; }
+
+inline __host__ __device__ int team_width(int dc_max) {
+  int w = 1;
+  while (w < dc_max) w <<= 1;
+  return w;
+}
+
+// FrameIO of frame b of a batch decode
+inline __device__ FrameIO batch_io(const DecodeArgs& a, int64_t b, int elem_bytes) {
+  FrameIO io;
+  const int64_t N = a.g.N;
+  io.llr = (const unsigned char*)a.llr + b * N * elem_bytes;
+  io.hard = a.hard ? a.hard + b * N : nullptr;
+  io.llr_out = a.llr_out ? a.llr_out + b * N : nullptr;
+  io.updates = a.updates ? a.updates + b : nullptr;
+  io.converged = a.converged ? a.converged + b : nullptr;
+  io.trace = a.trace ? a.trace + b * a.max_updates : nullptr;
+  io.max_updates = a.max_updates;
+  io.frame = a.frame_offset + (uint64_t)b;
+  return io;
+}
 
 inline __host__ __device__ int graph_smem_bytes(const GraphDesc& d) {
   if (d.is_qc) return align16(d.qc_words * 4);
@@ -114,7 +148,34 @@ inline __host__ __device__ FloodLayout flood_layout(int arith, int N, int E) {
   return l;
 }
 
+// Work queue of the persistent form (layout of ldpc_work_item_t).
+struct WorkItem {
+  int32_t code;
+  int32_t flags;
+  int64_t llr_offset;  // elements
+  int64_t out_offset;  // elements
+  int64_t max_updates;
+  uint64_t frame_index;
+};
+constexpr int kMaxQueueCodes = 16;
+
+struct QueueArgs {
+  DecodeArgs a;  // common parameters; llr/hard are base pointers, updates/converged per item
+  GraphDesc codes[kMaxQueueCodes];
+  int32_t n_codes;
+  const WorkItem* items;
+  int64_t n_items;
+  unsigned int* head;        // persistent mode: next item (zeroed before the launch)
+  int32_t persistent;        // 1: CTAs pop items until the queue is empty; 0: item = CTA index
+  int32_t graph_bytes;       // staged graph area (max over codes)
+  int32_t small_bytes;       // per-CTA working set (max over codes)
+  int32_t smem_state_bytes;  // frame state kept in shared memory when it fits this, else global
+};
+
 // Launchers (return a cudaError_t from the launch).
+cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int threads, int grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
 cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s);
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s);

@@ -129,7 +129,7 @@ def test_decode_validation_needs_no_gpu(lib):
     # batch 0 is a no-op
     assert lib.ldpc_decode(code._h, null, 0, ctypes.byref(p), null, null, null, null, null, null) == 0
     bad = [("schedule", 9), ("arith", 5), ("max_updates", -1), ("gamma", 1.5), ("llr_clip", 0.0),
-           ("reserved", 1), ("check_interval", -2)]
+           ("tune", 0x40), ("tune", 3), ("check_interval", -2)]
     for field, val in bad:
         q = L.make_params("lmd-cirbp", max_updates=10)
         setattr(q, field, val)
@@ -155,3 +155,28 @@ def test_default_params(lib):
     assert p.schedule == L.LMD_CIRBP and p.arith == L.FP32_SUMPRODUCT
     assert abs(p.gamma - 0.1) < 1e-12 and p.check_interval == 1 and p.llr_clip == 25.0
     assert lib.ldpc_default_params(None) == -1
+
+
+def test_queue_validation_needs_no_gpu(lib):
+    d = wl.design("bg2")
+    code = L.Code.from_protograph(d.shifts(16), 16, d.info_cols * 16, d.punct_cols)
+    null = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(64)
+    one = (ctypes.c_void_p * 1)(code._h)
+    p = L.make_params("me-lmd-cirbp")
+    q = lib.ldpc_decode_queue
+    assert q(one, 1, null, 0, null, ctypes.byref(p), null, null, null, L.QUEUE_PERSISTENT, null) == 0
+    assert q(one, 0, dummy, 1, dummy, ctypes.byref(p), null, null, null, 1, null) == -1  # no codes
+    assert q(one, 17, dummy, 1, dummy, ctypes.byref(p), null, null, null, 1, null) == -1
+    assert q(one, 1, dummy, 1, dummy, ctypes.byref(p), null, null, null, 2, null) == -1  # mode
+    assert q(one, 1, dummy, -1, dummy, ctypes.byref(p), null, null, null, 1, null) == -1
+    assert q(one, 1, dummy, 1 << 31, dummy, ctypes.byref(p), null, null, null, 1, null) == -5
+    assert q(one, 1, null, 1, dummy, ctypes.byref(p), null, null, null, 1, null) == -1  # no items
+    for sched in ["flooding", "rbp", "cirbp"]:
+        r = L.make_params(sched)
+        assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -5
+    r = L.make_params("me-cirbp", n_p=0)
+    assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
+    r = L.make_params("me-cirbp", tune=0x80)
+    assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
+    assert L.WORK_ITEM_DTYPE.itemsize == 40

@@ -1,0 +1,130 @@
+"""Persistent work-queue form (ldpc_decode_queue): frames of several lifted
+codes with per-frame budgets give the same results as batch decodes of each
+code, in persistent and static mode, and when replayed from a CUDA graph."""
+import numpy as np
+import pytest
+
+import paper_2102_11089_gb300 as L
+from paper_2102_11089_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _mixed_queue(arith, Zs=(16, 32, 64, 128), per=(6, 5, 4, 3), budgets=(1, 2), seed=3):
+    """Codes, a shuffled queue over them and the reference batch decodes."""
+    d = wl.bg2_like(3)
+    codes = [L.Code.from_protograph(d.shifts(Z), Z, d.info_cols * Z, d.punct_cols) for Z in Zs]
+    rng = np.random.default_rng(seed)
+    rows, llr_parts, off = [], [], 0
+    frame = 0
+    groups = []
+    for ci, (c, n) in enumerate(zip(codes, per)):
+        for bi, bit in enumerate(budgets):
+            lam = wl.seeded_llrs(c.N, n, wl.sigma2_from_ebn0(1.0 + 0.5 * bi, 0.2), 100 + 10 * ci + bi,
+                                 d.punct_mask(Zs[ci]))
+            x = wl.quantize_llrs(lam, 0.5) if arith == "int6" else lam
+            groups.append((ci, bit * c.E, frame, x, off))
+            for b in range(n):
+                rows.append((ci, off + b * c.N, off + b * c.N, bit * c.E, frame + b))
+            llr_parts.append(x.reshape(-1))
+            off += n * c.N
+            frame += n
+    order = rng.permutation(len(rows))
+    rows = [rows[i] for i in order]
+    cols = list(zip(*rows))
+    items = L.make_items(*[np.array(c) for c in cols])
+    llr = torch.from_numpy(np.concatenate(llr_parts)).cuda()
+    return codes, groups, rows, items, llr, off
+
+
+@pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "me-cirbp", "lmd-cirbp"])
+@pytest.mark.parametrize("arith", ["int6", "fp32"])
+def test_queue_equals_batch_decodes(schedule, arith):
+    codes, groups, rows, items, llr, total = _mixed_queue(arith)
+    p = L.make_params(schedule, arith, n_p=32, n_g=16, seed=9)
+    n = len(rows)
+    res = {}
+    for mode in [L.QUEUE_PERSISTENT, L.QUEUE_STATIC]:
+        hard = torch.full((total,), 7, dtype=torch.uint8, device="cuda")
+        upd = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        conv = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
+        L.decode_queue(codes, items, n, llr, p, hard=hard, updates=upd, converged=conv, mode=mode)
+        torch.cuda.synchronize()
+        res[mode] = (hard.cpu().numpy(), upd.cpu().numpy(), conv.cpu().numpy())
+    for k in range(3):
+        assert np.array_equal(res[L.QUEUE_PERSISTENT][k], res[L.QUEUE_STATIC][k])
+    hard, upd, conv = res[L.QUEUE_PERSISTENT]
+    pos = {r[4]: i for i, r in enumerate(rows)}  # frame index -> queue position
+    for ci, budget, f0, x, off in groups:
+        c = codes[ci]
+        pb = L.make_params(schedule, arith, n_p=32, n_g=16, seed=9, max_updates=budget, frame_offset=f0)
+        ref = L.decode(c, torch.from_numpy(np.ascontiguousarray(x)).cuda(), pb)
+        torch.cuda.synchronize()
+        for b in range(x.shape[0]):
+            i = pos[f0 + b]
+            assert upd[i] == ref["updates"][b].item(), (ci, b)
+            assert conv[i] == ref["converged"][b].item()
+            r0 = off + b * c.N
+            assert np.array_equal(hard[r0:r0 + c.N], ref["hard"][b].cpu().numpy())
+
+
+def test_queue_replays_from_cuda_graph():
+    codes, groups, rows, items, llr, total = _mixed_queue("fp32", Zs=(16, 64), per=(8, 4))
+    p = L.make_params("me-lmd-cirbp", "fp32", n_p=16, n_g=8, seed=1)
+    n = len(rows)
+    hard = torch.zeros((total,), dtype=torch.uint8, device="cuda")
+    upd = torch.zeros((n,), dtype=torch.int64, device="cuda")
+    conv = torch.zeros((n,), dtype=torch.uint8, device="cuda")
+    L.decode_queue(codes, items, n, llr, p, hard=hard, updates=upd, converged=conv)  # first use
+    torch.cuda.synchronize()
+    ref = (hard.clone(), upd.clone(), conv.clone())
+    hard.zero_(), upd.zero_(), conv.zero_()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            L.decode_queue(codes, items, n, llr, p, hard=hard, updates=upd, converged=conv)
+    for _ in range(2):
+        hard.zero_(), upd.zero_(), conv.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(hard, ref[0]) and torch.equal(upd, ref[1]) and torch.equal(conv, ref[2])
+
+
+def test_queue_rejects_tabular_codes():
+    c, v, m = wl.regular_code(96, 3, 6, 1)
+    code = L.Code.from_edges(c, v, m, 96, 48)
+    items = L.make_items(np.array([0]), np.array([0]), np.array([0]), np.array([10]), np.array([0]))
+    llr = torch.zeros(96, dtype=torch.float32, device="cuda")
+    with pytest.raises(L.LdpcError) as e:
+        L.decode_queue([code], items, 1, llr, L.make_params("me-lmd-cirbp"))
+    assert e.value.name == "LDPC_ERR_UNSUPPORTED"
+
+
+def test_queue_flags_item_with_bad_code_index():
+    d = wl.bg2_like(3)
+    code = L.Code.from_protograph(d.shifts(16), 16, d.info_cols * 16, d.punct_cols)
+    lam = wl.seeded_llrs(code.N, 2, wl.sigma2_from_ebn0(3.0, 0.2), 4, d.punct_mask(16))
+    llr = torch.from_numpy(lam.reshape(-1)).cuda()
+    items = L.make_items(np.array([0, 3]), np.array([0, code.N]), np.array([0, code.N]),
+                         np.array([code.E, code.E]), np.array([0, 1]))
+    upd = torch.full((2,), -1, dtype=torch.int64, device="cuda")
+    conv = torch.full((2,), 9, dtype=torch.uint8, device="cuda")
+    hard = torch.zeros(2 * code.N, dtype=torch.uint8, device="cuda")
+    L.decode_queue([code], items, 2, llr, L.make_params("me-lmd-cirbp"), hard=hard, updates=upd,
+                   converged=conv)
+    with pytest.raises(L.LdpcError) as e:
+        L.sync()
+    assert e.value.name == "LDPC_ERR_INVALID_ARG"
+    assert conv[1].item() == 2 and upd[1].item() == 0
+    assert conv[0].item() in (0, 1) and upd[0].item() > 0
+    L.sync()  # the status word was cleared
