@@ -95,7 +95,10 @@ typedef struct {
                                Sec. 2.A); flooding uses whole iterations only     */
     int64_t check_interval; /* syndrome checked at 0 updates and whenever the
                                count crosses a multiple of this (0 = never)       */
-    float llr_clip;         /* FP32: V2C inputs and C2V outputs clipped to +-this */
+    float llr_clip;         /* FP32: V2C inputs and C2V outputs clipped to +-this,
+                               in (0, 1e4]; the multi-edge schedules keep the
+                               sums L~ in fixed point with 2^-k resolution,
+                               k = min(24, 29 - floor(log2(dv_max * llr_clip))) */
     float q_step;           /* INT6: LLR value of one quantisation step (Delta)   */
     uint64_t seed;          /* Algorithm 4 random fill (Philox4x32-10 key)         */
     uint64_t frame_offset;  /* global index of frame 0 of this batch (Philox ctr)  */

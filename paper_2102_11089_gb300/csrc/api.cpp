@@ -489,7 +489,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
   if (p->max_updates < 0 || p->check_interval < 0) return fail(LDPC_ERR_INVALID_ARG, "negative budget");
   if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail(LDPC_ERR_INVALID_ARG, "gamma outside [0, 1]");
-  if (!(p->llr_clip > 0.0f && std::isfinite(p->llr_clip))) return fail(LDPC_ERR_INVALID_ARG, "llr_clip");
+  if (!(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
   if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 1024))
@@ -618,7 +618,7 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
     return fail(LDPC_ERR_UNSUPPORTED, "queue form: LMD-CIRBP, ME-CIRBP or ME-LMD-CIRBP");
   if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
-  if (p->check_interval < 0 || !(p->gamma >= 0.0 && p->gamma <= 1.0) || !(p->llr_clip > 0.0f) ||
+  if (p->check_interval < 0 || !(p->gamma >= 0.0 && p->gamma <= 1.0) || !(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f) ||
       (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad parameters");
   const bool me = p->schedule != LDPC_LMD_CIRBP;

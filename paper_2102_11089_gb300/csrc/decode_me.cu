@@ -9,9 +9,18 @@
 // (and every p) recomputes L~ and D.  Results do not depend on the order of
 // the parallel work.
 //
-// Checks are processed by teams of W lanes (W = power of two >= max check
-// degree): lane r of a team owns edge r of the check and gets the exclude-one
-// combination of eq. (2) (or min-sum) by W width-limited shuffles.
+// Work layout of one step (CTA of 256 or 512 threads):
+//  commit   a team of Wv lanes per selected p (Wv = power of two >= max VN
+//           degree): lane q reads edge q of p; team argmax of the residual,
+//           team sum of the new L_p.
+//  checks   a team of W lanes per affected check (W = power of two >= max
+//           check degree): lane r owns edge r; exclude-one combination of
+//           eq. (2) (or min-sum) by width-W shuffles.
+//  refresh  L~_j is kept as an exact integer sum: the 6-bit messages
+//           themselves, or FP32 messages in fixed point (x 2^k with k chosen so
+//           that d_v,max * llr_clip * 2^k < 2^30), updated by the checks
+//           phase with atomic deltas; integer sums do not depend on the order
+//           of the updates.  L~_j = lambda_j + that sum (x 2^-k).
 //
 // Algorithm 4 keeps the group index floor(D N_G) of every VN in shared memory.
 // Its random fill takes the fill-group members with the smallest keys (word
@@ -28,11 +37,12 @@ constexpr int kCap = 512;  // candidate list of the random fill
 
 // Big per-frame arrays (shared memory, or a global-memory slot for large codes)
 struct MEBig {
-  int C, P, lam, L, D, grp, par, total;
+  int C, P, lam, L, D, Lt, grp, par, total;
 };
-// Per-CTA working set of one step (always shared memory)
+// Per-CTA working set of one step (always shared memory).  The fill candidates
+// of Algorithm 4 share storage with the affected-check list (not live then).
 struct MESmall {
-  int sel, est, best, excl, cnl, cand, cnt, cntS, bits, touched, misc, total;
+  int sel, est, best, excl, cnl, cul, cbits, cnt, cntS, bits, touched, lbase, misc, total;
 };
 
 __host__ __device__ inline MEBig me_big(int arith, int M, int N, int E) {
@@ -46,25 +56,29 @@ __host__ __device__ inline MEBig me_big(int arith, int M, int N, int E) {
   l.lam = o; o = align16(o + N * llr);
   l.L = o; o = align16(o + N * llr);
   l.D = o; o = align16(o + N * dv);
+  l.Lt = o; o = align16(o + N * 4);
   l.grp = o; o = align16(o + N);
   l.par = o; o = align16(o + ((M + 31) / 32) * 4);
   l.total = o;
   return l;
 }
 
-__host__ __device__ inline MESmall me_small(int N, int n_p, int dvm, int n_g) {
+__host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int n_g) {
   MESmall l;
   int o = 0;
+  const int ncnl = n_p * (dvm > 1 ? dvm - 1 : 1);
   l.sel = o; o = align16(o + n_p * 4);
   l.est = o; o = align16(o + n_p * 4);
   l.best = o; o = align16(o + n_p * 8);
   l.excl = o; o = align16(o + n_p * 4);
-  l.cnl = o; o = align16(o + n_p * (dvm > 1 ? dvm - 1 : 1) * 8);
-  l.cand = o; o = align16(o + kCap * 8);
+  l.cnl = o; o = align16(o + (ncnl > kCap ? ncnl : kCap) * 8);
+  l.cul = o; o = align16(o + ncnl * 4);
+  l.cbits = o; o = align16(o + ((M + 31) / 32) * 4);
   l.cnt = o; o = align16(o + n_g * 4);
   l.cntS = o; o = align16(o + n_g * 4);
   l.bits = o; o = align16(o + ((N + 31) / 32) * 4);
   l.touched = o; o = align16(o + ((N + 31) / 32) * 4);
+  l.lbase = o; o = align16(o + 33 * 4);
   l.misc = o; o = align16(o + 32 * 4);
   l.total = o;
   return l;
@@ -73,7 +87,8 @@ __host__ __device__ inline MESmall me_small(int N, int n_p, int dvm, int n_g) {
 // shared scalars (misc area)
 struct MEMisc {
   int unsat;
-  int ncn;   // affected checks this step
+  int ncn;   // affected (check, owner) pairs this step
+  int ncu;   // distinct affected checks this step
   int nsel;  // selected VNs
   int npp;   // |P'| (ME-LMD)
   int kstar, fill_g, need, top;
@@ -92,20 +107,25 @@ struct MEState {
   L_* lam;
   L_* L;
   D_* D;
+  int32_t* Lt;   // sum over the edges of each VN of L~^C, exact integer (see top)
   uint8_t* grp;
   uint32_t* par;
   int32_t* sel;
   int32_t* est;
   unsigned long long* best;
   int32_t* excl;   // P' of ME-LMD-CIRBP (excluded from Algorithm 4's top-up)
-  int2* cnl;  // (check, owner k)
-  unsigned long long* cand;
-  int32_t* cnt;    // |G_i| over all VNs, kept up to date with grp
-  int32_t* cntS;   // per-group count of the VNs excluded from Algorithm 4's search set
-  uint32_t* bits;  // selection bitmap over VNs
-  uint32_t* touched;  // VNs whose D was rewritten in this step
+  int2* cnl;       // (check, owner k) of every affected check
+  int32_t* cul;     // distinct affected checks
+  unsigned long long* cand;  // aliases cnl
+  uint32_t* cbits;   // checks already listed this step
+  int32_t* cnt;      // |G_i| over all VNs, kept up to date with grp
+  int32_t* cntS;     // per-group count of the VNs excluded from Algorithm 4's search set
+  uint32_t* bits;    // selection bitmap over VNs
+  uint32_t* touched; // VNs whose D was rewritten in this step
+  int32_t* lbase;    // compaction: first selection slot of each lane's word range
   MEMisc* misc;
   const int16_t* tab;
+  float fx, ifx;     // FP32 fixed point: 2^k and 2^-k
 };
 
 __device__ __forceinline__ void philox4(uint32_t c[4], uint64_t seed) {
@@ -127,11 +147,24 @@ __device__ __forceinline__ void philox4(uint32_t c[4], uint64_t seed) {
 __device__ __forceinline__ float ci_me(const MEState<kFP32>&, float a, float b) { return ci_fp(a, b); }
 __device__ __forceinline__ uint16_t ci_me(const MEState<kINT6>& s, int a, int b) { return ci_int(a, b, s.tab); }
 
+// message -> exact integer term of the L~ sum, and the sum -> L~ contribution
+__device__ __forceinline__ int fix_msg(const MEState<kFP32>& s, float x) { return __float2int_rn(x * s.fx); }
+__device__ __forceinline__ int fix_msg(const MEState<kINT6>&, int8_t x) { return (int)x; }
+__device__ __forceinline__ float lt_total(const MEState<kFP32>& s, int n) { return s.lam[n] + (float)s.Lt[n] * s.ifx; }
+__device__ __forceinline__ int16_t lt_total(const MEState<kINT6>& s, int n) { return (int16_t)(s.lam[n] + s.Lt[n]); }
+
 // Algorithm 4 line 2: group i = floor(D N_G), clamped to N_G - 1
 __device__ __forceinline__ int group_of(float d, int ng) { return min((int)floorf(d * (float)ng), ng - 1); }
 __device__ __forceinline__ int group_of(uint16_t d, int ng) { return min((int)(((int)d * ng) / 65534), ng - 1); }
 
-__device__ __forceinline__ bool in_bits(const uint32_t* bits, int n) { return (bits[n >> 5] >> (n & 31)) & 1u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+// cnt[idx] += v from the lanes of `mask` (the calling lanes; all of them must
+// call), one atomic per distinct idx.
+__device__ __forceinline__ void agg_add(int32_t* cnt, int idx, int v, unsigned mask) {
+  const unsigned peers = __match_any_sync(mask, idx);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[idx], v * __popc(peers));
+}
 
 // Algorithm 4 over S = O_N minus nexcl excluded VNs (their bits are set and
 // s.cntS counts them per group): sets the bits of the selected VNs (at most
@@ -139,12 +172,11 @@ __device__ __forceinline__ bool in_bits(const uint32_t* bits, int n) { return (b
 template <int A>
 __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint32_t step, uint64_t frame,
                      uint64_t seed) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   MEMisc* ms = s.misc;
-  if ((tid >> 5) == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S (one warp)
+  if (warp == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S (one warp)
     // |G_i| over S = cnt[i] - cntS[i] (cntS counts the excluded VNs per group);
     // lane l of chunk b looks at group ng - 1 - (b + l), i.e. k = b + l + 1
-    const int lane = tid & 31;
     const int sz = N - nexcl;
     int kstar = 0, q = 0;
     if (sz <= np) {
@@ -175,16 +207,20 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
       ms->fill_g = ng - kstar - 1;
       ms->thr = 0xffffffffu;
       if (need > 0) {
+        // first threshold: need + 3 sqrt(need) + 8 expected members at or below
+        // it, short of `need` with probability < 1e-3 (the selection does not
+        // depend on it)
         const int fg = ng - kstar - 1;
         const int members = s.cnt[fg] - s.cntS[fg];
-        const unsigned long long want = (unsigned long long)(3 * need / 2 + 48);
-        if (members > kCap / 2)
-          ms->thr = (uint32_t)min(0xffffffffull, (want << 32) / (unsigned long long)members);
+        if (members > kCap / 2) {
+          const float want = (float)need + 3.0f * sqrtf((float)need) + 8.0f;
+          const float t = want / (float)members * 4294967296.0f;
+          ms->thr = t >= 4294967040.0f ? 0xffffffffu : (uint32_t)t;
+        }
       }
       ms->lo = 0;
       ms->hi = 0xffffffffu;
       ms->hi_set = 0;
-      ms->done = need == 0;
       ms->ncand = 0;
     }
   }
@@ -194,52 +230,61 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
   const uint32_t* grp4 = (const uint32_t*)s.grp;
   // one pass over VN quads: line 3 selects Q(k*); lines 4-6 gather fill candidates
   // (key = word i of the Philox block of quad q)
+  bool fill = need > 0;
   for (int iter = 0; iter < 64; ++iter) {
     const uint32_t thr = ms->thr;
-    const bool fill = !ms->done;
-    for (int q = tid; q < nq; q += nt) {
-      const uint32_t g4 = grp4[q];
-      const unsigned ex = (s.bits[q >> 3] >> ((q & 7) * 4)) & 0xfu;
+    for (int q0 = warp * 32; q0 < nq; q0 += nt) {  // warp-uniform trip count
+      const int q = q0 + lane;
       unsigned fm = 0;
+      if (q < nq) {
+        const uint32_t g4 = grp4[q];
+        const unsigned ex = (s.bits[q >> 3] >> ((q & 7) * 4)) & 0xfu;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int n = 4 * q + i;
-        if (n >= N || ((ex >> i) & 1u)) continue;
-        const int gi = (int)((g4 >> (8 * i)) & 0xffu);
-        if (iter == 0 && gi >= top) atomicOr(&s.bits[n >> 5], 1u << (n & 31));
-        if (gi == fg) fm |= 1u << i;
+        for (int i = 0; i < 4; ++i) {
+          const int n = 4 * q + i;
+          if (n >= N || ((ex >> i) & 1u)) continue;
+          const int gi = (int)((g4 >> (8 * i)) & 0xffu);
+          if (iter == 0 && gi >= top) atomicOr(&s.bits[n >> 5], 1u << (n & 31));
+          if (gi == fg) fm |= 1u << i;
+        }
       }
-      if (!fill || !fm) continue;
+      if (!fill) continue;
       uint32_t w[4] = {(uint32_t)q, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
-      philox4(w, seed);
+      if (fm) philox4(w, seed);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (!((fm >> i) & 1u) || w[i] > thr) continue;
-        const int pos = atomicAdd(&ms->ncand, 1);
-        if (pos < kCap) s.cand[pos] = ((unsigned long long)w[i] << 32) | (unsigned)(4 * q + i);
+        const bool c = ((fm >> i) & 1u) && w[i] <= thr;
+        const unsigned bal = __ballot_sync(kFull, c);
+        if (!bal) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ms->ncand, __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        const int pos = base + __popc(bal & lanemask_lt());
+        if (c && pos < kCap) s.cand[pos] = ((unsigned long long)w[i] << 32) | (unsigned)(4 * q + i);
       }
     }
     __syncthreads();
     if (!fill) break;
     const int nc = ms->ncand;
-    const bool ok = nc >= need && nc <= kCap;
-    if (ok) {
-      // exact rank among the candidates: (key, n) is unique
-      for (int c = tid; c < nc; c += nt) {
+    if (nc >= need && nc <= kCap) {
+      // exact rank among the candidates ((key, n) is unique): a warp per
+      // candidate, its lanes splitting the comparisons
+      for (int c = warp; c < nc; c += nw) {
         const unsigned long long kc = s.cand[c];
         int rank = 0;
-        for (int c2 = 0; c2 < nc; ++c2) rank += s.cand[c2] < kc;
-        if (rank < need) {
+        for (int c2 = lane; c2 < nc; c2 += 32) rank += s.cand[c2] < kc;
+        rank = __reduce_add_sync(kFull, rank);
+        if (lane == 0 && rank < need) {
           const int n = (int)(kc & 0xffffffffull);
           atomicOr(&s.bits[n >> 5], 1u << (n & 31));
         }
       }
+      __syncthreads();
+      break;
     }
-    __syncthreads();
+    __syncthreads();  // every thread has read ncand
     if (tid == 0) {
-      if (ok) {
-        ms->done = 1;
-      } else if (nc < need) {  // bisect the threshold upwards
+      if (nc < need) {  // bisect the threshold upwards
         ms->lo = thr;
         ms->thr = ms->hi_set ? thr + (ms->hi - thr + 1) / 2
                              : (thr > 0x7fffffffu ? 0xffffffffu : 2u * thr + 1u);
@@ -251,41 +296,45 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
       ms->ncand = 0;
     }
     __syncthreads();
-    if (ms->done) break;
   }
 }
 
-// Compact the selection bitmap into s.sel (ascending); the next step clears it.
+// Compact the selection bitmap into s.sel (ascending), at most np entries; the
+// next step clears the bitmap.  Warp 0 splits the words into 32 ranges and
+// scans their counts; then every warp expands ranges, a lane per bit.
 template <int A>
 __device__ void compact_selection(int N, const MEState<A>& s, int np) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int words = (N + 31) / 32;
+  const int per = (words + 31) / 32;
   if (warp == 0) {
-    int base = 0;
-    for (int w0 = 0; w0 < words; w0 += 32) {
-      const int w = w0 + lane;
-      const uint32_t bw = w < words ? s.bits[w] : 0u;
-      const int c = __popc(bw);
-      int incl = c;
+    const int w0 = lane * per, w1 = min(words, w0 + per);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(s.bits[w]);
+    int incl = c;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-      }
-      int pos = base + incl - c;
-      uint32_t x = bw;
-      while (x) {
-        const int bit = __ffs(x) - 1;
-        x &= x - 1;
-        if (pos < np) s.sel[pos] = w * 32 + bit;
-        ++pos;
-      }
-      base += __shfl_sync(kFull, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (lane == 0) {
-      s.misc->nsel = min(base, np);
+    s.lbase[lane] = incl - c;
+    if (lane == 31) {
+      s.misc->nsel = min(incl, np);
       s.misc->ncn = 0;
+      s.misc->ncu = 0;
       s.misc->npp = 0;
+    }
+  }
+  __syncthreads();
+  for (int l = warp; l < 32; l += nw) {
+    int pos = s.lbase[l];
+    if (pos >= np) continue;
+    const int w0 = l * per, w1 = min(words, w0 + per);
+    for (int w = w0; w < w1 && pos < np; ++w) {
+      const uint32_t bw = s.bits[w];
+      const int at = pos + __popc(bw & lanemask_lt());
+      if (((bw >> lane) & 1u) && at < np) s.sel[at] = w * 32 + lane;
+      pos += __popc(bw);
     }
   }
   __syncthreads();
@@ -302,13 +351,14 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
   const int N = gd.N, E = gd.E, M = gd.M;
   const int np = a.n_p, ng = a.n_g;
   const MEBig lb = me_big(A, M, N, E);
-  const MESmall ls = me_small(N, np, gd.dv_max, ng);
+  const MESmall ls = me_small(M, N, np, gd.dv_max, ng);
   MEState<A> s;
   s.C = (M_*)(big + lb.C);
   s.P = (M_*)(big + lb.P);
   s.lam = (L_*)(big + lb.lam);
   s.L = (L_*)(big + lb.L);
   s.D = (D_*)(big + lb.D);
+  s.Lt = (int32_t*)(big + lb.Lt);
   s.grp = (uint8_t*)(big + lb.grp);
   s.par = (uint32_t*)(big + lb.par);
   s.sel = (int32_t*)(small + ls.sel);
@@ -316,17 +366,28 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
   s.best = (unsigned long long*)(small + ls.best);
   s.excl = (int32_t*)(small + ls.excl);
   s.cnl = (int2*)(small + ls.cnl);
-  s.cand = (unsigned long long*)(small + ls.cand);
+  s.cul = (int32_t*)(small + ls.cul);
+  s.cand = (unsigned long long*)(small + ls.cnl);
+  s.cbits = (uint32_t*)(small + ls.cbits);
   s.cnt = (int32_t*)(small + ls.cnt);
   s.cntS = (int32_t*)(small + ls.cntS);
   s.bits = (uint32_t*)(small + ls.bits);
   s.touched = (uint32_t*)(small + ls.touched);
+  s.lbase = (int32_t*)(small + ls.lbase);
   s.misc = (MEMisc*)(small + ls.misc);
   s.tab = tab_int;
+  {
+    // fixed point of the FP32 L~ sums: d_v,max * llr_clip * 2^k < 2^30
+    const int k = min(24, 29 - ilogbf((float)gd.dv_max * a.llr_clip));
+    s.fx = __int_as_float((127 + k) << 23);
+    s.ifx = __int_as_float((127 - k) << 23);
+  }
   MEMisc* ms = s.misc;
   const float clip = a.llr_clip;
   const uint64_t frame = io.frame;
   const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
+  const int Wv = team_width(gd.dv_max), tpv = 32 / Wv, vteam = lane / Wv, q = lane % Wv;
+  const int Mw = (M + 31) / 32, Nw = (N + 31) / 32;
 
   int bad = 0;
   for (int n = tid; n < N; n += nt) {
@@ -344,8 +405,11 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
     s.L[n] = v;
   }
   for (int e = tid; e < E; e += nt) s.C[e] = (M_)0;
-  for (int w = tid; w < (N + 31) / 32; w += nt) s.bits[w] = 0u;
-  for (int w = tid; w < (M + 31) / 32; w += nt) s.par[w] = 0u;
+  for (int w = tid; w < Nw; w += nt) s.bits[w] = 0u;
+  for (int w = tid; w < Mw; w += nt) {
+    s.par[w] = 0u;
+    s.cbits[w] = 0u;
+  }
   for (int i = tid; i < ng; i += nt) {
     s.cnt[i] = 0;
     s.cntS[i] = 0;
@@ -353,6 +417,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
   if (tid == 0) {
     ms->unsat = 0;
     ms->ncn = 0;
+    ms->ncu = 0;
     ms->npp = 0;
   }
   if (__syncthreads_or(bad)) {
@@ -382,13 +447,26 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
     }
   }
   __syncthreads();
-  for (int n = tid; n < N; n += nt) {
-    const L_ lt = vn_total<A, G>(g, s.lam, s.P, n);
-    const D_ d = ci_me(s, s.L[n], lt);
-    const int gi = group_of(d, ng);
-    s.D[n] = d;
-    s.grp[n] = (uint8_t)gi;
-    atomicAdd(&s.cnt[gi], 1);
+  for (int n0 = warp * 32; n0 < N; n0 += nt) {  // warp-uniform trip count
+    const int n = n0 + lane;
+    const bool act = n < N;
+    int gi = 0;
+    if (act) {
+      const typename G::V v = g.vn(n);
+      int acc = 0;
+      for (int k = 0; k < v.d; ++k) {
+        int e, m;
+        g.vedge(v, k, e, m);
+        acc += fix_msg(s, s.P[e]);
+      }
+      s.Lt[n] = acc;
+      const D_ d = ci_me(s, s.L[n], lt_total(s, n));
+      gi = group_of(d, ng);
+      s.D[n] = d;
+      s.grp[n] = (uint8_t)gi;
+    }
+    const unsigned am = __ballot_sync(kFull, act);
+    if (act) agg_add(s.cnt, gi, 1, am);
   }
   __syncthreads();
 
@@ -399,92 +477,160 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
     alg4<A>(s, N, np, ng, 0, step, frame, a.seed);
     compact_selection<A>(N, s, np);
   }
+  // L~_j, D_j of VN j (j < 0: idle lane) unless already rewritten in this
+  // step; group and group sizes follow.  All lanes of the warp call it.
+  auto refresh_vn = [&](int j) {
+    bool ch = false;
+    int go = 0, gn = 0;
+    if (j >= 0) {
+      const uint32_t bit = 1u << (j & 31);
+      if (!(atomicOr(&s.touched[j >> 5], bit) & bit)) {
+        const D_ d = ci_me(s, s.L[j], lt_total(s, j));
+        s.D[j] = d;
+        gn = group_of(d, ng);
+        go = s.grp[j];
+        if (gn != go) {
+          s.grp[j] = (uint8_t)gn;
+          ch = true;
+        }
+      }
+    }
+    const unsigned cm = __ballot_sync(kFull, ch);
+    if (ch) {
+      agg_add(s.cnt, go, -1, cm);
+      agg_add(s.cnt, gn, 1, cm);
+    }
+  };
   while (!stop && count < io.max_updates) {
     int nsel = ms->nsel;
     if (nsel <= 0) break;  // nothing selectable: the step would not advance
     if ((int64_t)nsel > io.max_updates - count) nsel = (int)(io.max_updates - count);
-    // -- for each selected p: m*_p = argmax_i R_{i->p} on the pre-step state (the
-    //    edges of p are disjoint from every other p's), commit L^C <- L~^C, L_p,
-    //    syndrome, trace, the checks i in M(p)\m*_p whose inputs changed
-    for (int w = tid; w < (N + 31) / 32; w += nt) {
+    // -- for each selected p (a team of Wv lanes, lane q on edge q of p):
+    //    m*_p = argmax_i R_{i->p} on the pre-step state (the edges of p are
+    //    disjoint from every other p's), commit L^C <- L~^C, L_p, syndrome,
+    //    trace, and list the checks i in M(p)\m*_p whose inputs changed
+    for (int w = tid; w < Nw; w += nt) {
       s.bits[w] = 0u;
       s.touched[w] = 0u;
     }
     for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
-    for (int k = tid; k < nsel; k += nt) {
-      const int p = s.sel[k];
-      const typename G::V v = g.vn(p);
+    for (int k0 = warp * tpv; k0 < nsel; k0 += nw * tpv) {  // warp-uniform trip count
+      const int k = k0 + vteam;
+      const bool act = k < nsel;
+      int p = 0, dv = 0, e = 0, m = 0;
       uint32_t bk = 0, bi = 0xffffffffu;
-      for (int q = 0; q < v.d; ++q) {
-        int e, m;
-        g.vedge(v, q, e, m);
-        am_update(bk, bi, rkey(s.P[e], s.C[e]), (uint32_t)e);
-      }
-      const int es = (int)bi;
-      s.est[k] = es;
-      s.best[k] = 0ull;
-      s.C[es] = s.P[es];
-      const L_ lold = s.L[p];
-      const L_ lnew = vn_total<A, G>(g, s.lam, s.C, p);
-      s.L[p] = lnew;
-      const bool flip = (lold < (L_)0) != (lnew < (L_)0);
-      for (int q = 0; q < v.d; ++q) {
-        int e, m;
-        g.vedge(v, q, e, m);
-        if (flip) {  // tentative decision of p flipped: parity of every check of p
-          const uint32_t bit = 1u << (m & 31);
-          const uint32_t old = atomicXor(&s.par[m >> 5], bit);
-          atomicAdd(&ms->unsat, (old & bit) ? -1 : 1);
-        }
-        if (e != es) {
-          const int pos = atomicAdd(&ms->ncn, 1);
-          s.cnl[pos] = make_int2(m, k);
+      M_ pk = (M_)0, ck = (M_)0;
+      if (act) {
+        p = s.sel[k];
+        const typename G::V v = g.vn(p);
+        dv = v.d;
+        if (q < dv) {
+          g.vedge(v, q, e, m);
+          pk = s.P[e];
+          ck = s.C[e];
+          bk = rkey(pk, ck);
+          bi = (uint32_t)e;
         }
       }
-      if (io.trace) io.trace[count + k] = es;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {  // team argmax, ties to the lower edge id
+        if (o >= Wv) continue;
+        const uint32_t ok = __shfl_xor_sync(kFull, bk, o), oi = __shfl_xor_sync(kFull, bi, o);
+        if (ok > bk || (ok == bk && oi < bi)) {
+          bk = ok;
+          bi = oi;
+        }
+      }
+      const bool mine = act && q < dv;
+      const bool isbest = mine && (uint32_t)e == bi;
+      if (isbest) s.C[e] = pk;
+      // L_p = lambda_p + sum of the committed C2V of p (butterfly sum: the same
+      // value in every lane of the team)
+      L_ lnew;
+      if (A == kFP32) {
+        float x = mine ? (float)(isbest ? pk : ck) : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          if (o < Wv) x += __shfl_xor_sync(kFull, x, o);
+        lnew = act ? (L_)((float)s.lam[p] + x) : (L_)0;
+      } else {
+        int x = mine ? (int)(isbest ? pk : ck) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          if (o < Wv) x += __shfl_xor_sync(kFull, x, o);
+        lnew = act ? (L_)((int)s.lam[p] + x) : (L_)0;
+      }
+      int flip = 0;
+      if (act && q == 0) {
+        const L_ lold = s.L[p];
+        flip = (lold < (L_)0) != (lnew < (L_)0);
+        s.L[p] = lnew;
+        s.est[k] = (int)bi;
+        s.best[k] = 0ull;
+        if (io.trace) io.trace[count + k] = (int)bi;
+      }
+      flip = __shfl_sync(kFull, flip, vteam * Wv);
+      int du = 0;
+      if (flip && mine) {  // tentative decision of p flipped: parity of every check of p
+        const uint32_t bit = 1u << (m & 31);
+        const uint32_t old = atomicXor(&s.par[m >> 5], bit);
+        du = (old & bit) ? -1 : 1;
+      }
+      du = __reduce_add_sync(kFull, du);
+      if (lane == 0 && du != 0) atomicAdd(&ms->unsat, du);
+      const bool aff = mine && !isbest;
+      bool first = false;
+      if (aff) {
+        const uint32_t bit = 1u << (m & 31);
+        first = !(atomicOr(&s.cbits[m >> 5], bit) & bit);
+      }
+      const unsigned bal = __ballot_sync(kFull, aff);
+      if (bal) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ms->ncn, __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (aff) s.cnl[base + __popc(bal & lanemask_lt())] = make_int2(m, k);
+      }
+      const unsigned bf = __ballot_sync(kFull, first);
+      if (bf) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ms->ncu, __popc(bf));
+        base = __shfl_sync(kFull, base, 0);
+        if (first) s.cul[base + __popc(bf & lanemask_lt())] = m;
+      }
     }
     __syncthreads();
-    const int ncn = ms->ncn;
-    // -- precomputed C2V of every affected check
-    for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
+    const int ncn = ms->ncn, ncu = ms->ncu;
+    // -- precomputed C2V of every affected check (once per check); the L~ sums
+    //    of its variables follow by exact deltas
+    for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
       const int t = t0 + team;
+      const int m = t < ncu ? s.cul[t] : -1;
       int e, j;
       M_ out;
-      const int dc = team_c2v<A, G>(g, s.C, s.L, t < ncn ? s.cnl[t].x : -1, r, W, clip, e, j, out);
-      if (r < dc) s.P[e] = out;
+      const int dc = team_c2v<A, G>(g, s.C, s.L, m, r, W, clip, e, j, out);
+      if (r < dc) {
+        const int delta = fix_msg(s, out) - fix_msg(s, s.P[e]);
+        s.P[e] = out;
+        if (delta != 0) atomicAdd(&s.Lt[j], delta);
+      }
     }
     __syncthreads();
-    // -- L~_j, D_j next to affected checks and of every p; the first writer of a
-    //    VN in this step updates its group and the group sizes; LMD candidates
-    auto refresh_vn = [&](int j) -> D_ {
-      const L_ lt = vn_total<A, G>(g, s.lam, s.P, j);
-      const D_ d = ci_me(s, s.L[j], lt);
-      const uint32_t bit = 1u << (j & 31);
-      if (!(atomicOr(&s.touched[j >> 5], bit) & bit)) {
-        s.D[j] = d;
-        const int gn = group_of(d, ng), go = s.grp[j];
-        if (gn != go) {
-          s.grp[j] = (uint8_t)gn;
-          atomicSub(&s.cnt[go], 1);
-          atomicAdd(&s.cnt[gn], 1);
-        }
-      }
-      return d;
-    };
-    for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
+    // -- L~_j, D_j next to the affected checks and of every p
+    for (int w = tid; w < Mw; w += nt) s.cbits[w] = 0u;
+    for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
       const int t = t0 + team;
-      if (t >= ncn) continue;
-      const int2 ck = s.cnl[t];
-      const typename G::C cc = g.cn(ck.x);
-      if (r >= cc.d) continue;
-      const int j = g.cvn(cc, r);
-      const D_ d = refresh_vn(j);
-      if (SCHED == kMELMD && j != s.sel[ck.y]) {
-        const unsigned long long key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
-        atomicMax(&s.best[ck.y], key);
+      int j = -1;
+      if (t < ncu) {
+        const typename G::C cc = g.cn(s.cul[t]);
+        if (r < cc.d) j = g.cvn(cc, r);
       }
+      refresh_vn(j);
     }
-    for (int k = tid; k < nsel; k += nt) refresh_vn(s.sel[k]);
+    for (int k0 = warp * 32; k0 < nsel; k0 += nt) {
+      const int k = k0 + lane;
+      refresh_vn(k < nsel ? s.sel[k] : -1);
+    }
     __syncthreads();
     count += nsel;
     ++step;
@@ -497,27 +643,64 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
       compact_selection<A>(N, s, np);
       continue;
     }
-    // -- Alg. 6 lines 6-10: P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of
-    //    Sec. 5.A: N(m*_p)\p), de-duplicated in the selection bitmap
-    for (int k = tid; k < nsel; k += nt) {
-      const int p = s.sel[k];
-      unsigned long long bk = s.best[k];
-      if (g.vn(p).d == 1) {
-        const typename G::C cc = g.cn(g.ecn(s.est[k]));
-        bk = 0ull;
-        for (int q = 0; q < cc.d; ++q) {
-          const int j = g.cvn(cc, q);
-          if (j == p) continue;
-          const unsigned long long key = ((unsigned long long)mkey(s.D[j]) << 32) | (0xffffffffu - (uint32_t)j);
-          bk = key > bk ? key : bk;
+    // -- Alg. 6 lines 6-10, candidates: per (check i, owner p) the best
+    //    j in N(i)\p by (D_j, lower index)
+    for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
+      const int t = t0 + team;
+      unsigned long long key = 0ull;
+      int k = 0;
+      if (t < ncn) {
+        const int2 ck = s.cnl[t];
+        k = ck.y;
+        const typename G::C cc = g.cn(ck.x);
+        if (r < cc.d) {
+          const int j = g.cvn(cc, r);
+          if (j != s.sel[k]) key = ((unsigned long long)mkey(s.D[j]) << 32) | (0xffffffffu - (uint32_t)j);
         }
       }
-      if (bk == 0ull) continue;  // empty candidate set
-      const int j = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
-      const uint32_t bit = 1u << (j & 31);
-      if (!(atomicOr(&s.bits[j >> 5], bit) & bit)) {
-        s.excl[atomicAdd(&ms->npp, 1)] = j;
-        atomicAdd(&s.cntS[s.grp[j]], 1);  // per-group count of P' for Algorithm 4's top-up
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        if (o >= W) continue;
+        const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
+        key = ok > key ? ok : key;
+      }
+      if (r == 0 && key != 0ull) atomicMax(&s.best[k], key);
+    }
+    __syncthreads();
+    // -- P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of Sec. 5.A:
+    //    N(m*_p)\p), de-duplicated in the selection bitmap
+    for (int k0 = warp * 32; k0 < nsel; k0 += nt) {  // warp-uniform trip count
+      const int k = k0 + lane;
+      bool add = false;
+      int j = 0;
+      if (k < nsel) {
+        const int p = s.sel[k];
+        unsigned long long bk = s.best[k];
+        if (g.vn(p).d == 1) {
+          const typename G::C cc = g.cn(g.ecn(s.est[k]));
+          bk = 0ull;
+          for (int qq = 0; qq < cc.d; ++qq) {
+            const int jj = g.cvn(cc, qq);
+            if (jj == p) continue;
+            const unsigned long long key = ((unsigned long long)mkey(s.D[jj]) << 32) | (0xffffffffu - (uint32_t)jj);
+            bk = key > bk ? key : bk;
+          }
+        }
+        if (bk != 0ull) {  // else an empty candidate set
+          j = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
+          const uint32_t bit = 1u << (j & 31);
+          add = !(atomicOr(&s.bits[j >> 5], bit) & bit);
+        }
+      }
+      const unsigned am = __ballot_sync(kFull, add);
+      if (am) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ms->npp, __popc(am));
+        base = __shfl_sync(kFull, base, 0);
+        if (add) {
+          s.excl[base + __popc(am & lanemask_lt())] = j;
+          agg_add(s.cntS, s.grp[j], 1, am);  // per-group count of P' for Algorithm 4's top-up
+        }
       }
     }
     __syncthreads();
@@ -637,7 +820,7 @@ cudaError_t launch_me_queue_tpb(const QueueArgs& q, int grid, size_t smem, cudaS
 
 template <int A, int S, class G, int TPB>
 cudaError_t launch_me_tpb(const DecodeArgs& a, cudaStream_t st) {
-  const MESmall ls = me_small(a.g.N, a.n_p, a.g.dv_max, a.n_g);
+  const MESmall ls = me_small(a.g.M, a.g.N, a.n_p, a.g.dv_max, a.n_g);
   if (a.gstate) {
     const size_t smem = (size_t)a.graph_smem + (size_t)ls.total;
     auto k = me_decode_kernel_gs<A, S, G, TPB>;
@@ -687,7 +870,7 @@ size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int 
 }
 
 size_t me_smem_per_cta(const GraphDesc& g, int n_p, int n_g) {
-  return (size_t)me_small(g.N, n_p, g.dv_max, n_g).total;
+  return (size_t)me_small(g.M, g.N, n_p, g.dv_max, n_g).total;
 }
 
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s) {

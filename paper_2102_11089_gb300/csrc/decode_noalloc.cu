@@ -77,7 +77,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
   if (p->max_updates < 0 || p->check_interval < 0) return fail(LDPC_ERR_INVALID_ARG, "negative budget");
   if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail(LDPC_ERR_INVALID_ARG, "gamma outside [0, 1]");
-  if (!(p->llr_clip > 0.0f && std::isfinite(p->llr_clip))) return fail(LDPC_ERR_INVALID_ARG, "llr_clip");
+  if (!(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
   if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 255))

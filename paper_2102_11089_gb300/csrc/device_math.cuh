@@ -136,30 +136,41 @@ __device__ __forceinline__ int team_c2v(const G& g, const typename Arith<A>::msg
       j = g.cvn(cc, r);
     }
   }
+  // exclude-one combination: inclusive prefix and suffix scans over the team,
+  // lane r takes prefix(r - 1) (+) suffix(r + 1); the sign is the team parity
+  // with r's own sign removed
   if (A == kFP32) {
     const float enc = r < dc ? encode_fp((float)L[j] - (float)C[e], clip) : 0.0f;
-    float sum = 0.0f;
-    unsigned neg = 0;
-    for (int k = 0; k < W; ++k) {
-      const float v = __shfl_sync(kFull, enc, k, W);
-      if (k != r && k < dc) {
-        sum += fabsf(v);
-        neg ^= __float_as_uint(v) >> 31;
-      }
+    const unsigned sg = __float_as_uint(enc) >> 31;
+    unsigned sall = sg;
+    float pre = fabsf(enc), suf = pre;
+    for (int o = 1; o < W; o <<= 1) {
+      sall ^= __shfl_xor_sync(kFull, sall, o);
+      const float u = __shfl_up_sync(kFull, pre, o, W);
+      const float d = __shfl_down_sync(kFull, suf, o, W);
+      if (r >= o) pre += u;
+      if (r + o < W) suf += d;
     }
-    out = (typename Arith<A>::msg)combine_fp(sum, neg, clip);
+    const float pl = __shfl_up_sync(kFull, pre, 1, W);
+    const float sr = __shfl_down_sync(kFull, suf, 1, W);
+    const float sum = (r > 0 ? pl : 0.0f) + (r + 1 < W ? sr : 0.0f);
+    out = (typename Arith<A>::msg)combine_fp(sum, sall ^ sg, clip);
   } else {
     const int enc = r < dc ? (int)encode_int((int)L[j] - (int)C[e]) : 0;
-    int mag = 31;
-    unsigned neg = 0;
-    for (int k = 0; k < W; ++k) {
-      const int v = __shfl_sync(kFull, enc, k, W);
-      if (k != r && k < dc) {
-        neg ^= (v < 0);
-        mag = min(mag, abs(v));
-      }
+    const unsigned sg = enc < 0;
+    unsigned sall = sg;
+    int pre = r < dc ? abs(enc) : 31, suf = pre;
+    for (int o = 1; o < W; o <<= 1) {
+      sall ^= __shfl_xor_sync(kFull, sall, o);
+      const int u = __shfl_up_sync(kFull, pre, o, W);
+      const int d = __shfl_down_sync(kFull, suf, o, W);
+      if (r >= o) pre = min(pre, u);
+      if (r + o < W) suf = min(suf, d);
     }
-    out = (typename Arith<A>::msg)(neg ? -mag : mag);
+    const int pl = __shfl_up_sync(kFull, pre, 1, W);
+    const int sr = __shfl_down_sync(kFull, suf, 1, W);
+    const int mag = min(r > 0 ? pl : 31, r + 1 < W ? sr : 31);
+    out = (typename Arith<A>::msg)((sall ^ sg) ? -mag : mag);
   }
   return dc;
 }

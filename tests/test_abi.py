@@ -128,7 +128,7 @@ def test_decode_validation_needs_no_gpu(lib):
     dummy = ctypes.c_void_p(16)
     # batch 0 is a no-op
     assert lib.ldpc_decode(code._h, null, 0, ctypes.byref(p), null, null, null, null, null, null) == 0
-    bad = [("schedule", 9), ("arith", 5), ("max_updates", -1), ("gamma", 1.5), ("llr_clip", 0.0),
+    bad = [("schedule", 9), ("arith", 5), ("max_updates", -1), ("gamma", 1.5), ("llr_clip", 0.0), ("llr_clip", 2e4),
            ("tune", 0x40), ("tune", 3), ("check_interval", -2)]
     for field, val in bad:
         q = L.make_params("lmd-cirbp", max_updates=10)
