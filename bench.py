@@ -49,6 +49,10 @@ def parse():
                     help="generate one batch with the channel kernel and time --reps decode launches "
                          "(the command the ncu captures under profiles/ use)")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--queue-frames", type=int, default=6144,
+                    help="frames of the mixed-lifting BG2-shaped queue comparison (extras)")
+    ap.add_argument("--queue-only", action="store_true",
+                    help="run only the mixed-lifting queue comparison and print its JSON")
     return ap.parse_args()
 
 
@@ -465,7 +469,174 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
     ms_se, o_se = time_decode(L, code, x[:B3].contiguous(), p_se, reps=1)
     res["single_edge_lmd_cirbp"] = {"frames": B3, "fer": fer_of(o_se), "ms": ms_se,
                                     "gbit_s": B3 * code.K / (ms_se * 1e-3) / 1e9}
+    if args.queue_frames > 0:
+        res["queue_mixed_bg2"] = run_queue_mixed(args, L, device)
     return res
+
+
+QUEUE_ZS = (16, 32, 64, 128, 256, 384)
+
+
+def mixed_bg2(L, device, frames, arith="fp32", seed=3):
+    """Frames of the BG2-shaped code (42x52 protograph, 2 punctured columns) at
+    lifting sizes drawn uniformly from 16..384, Eb/N0 ~ U[0.5, 3.0] dB and an
+    update budget ~ U{2..20} x E per frame.  Frames are stored grouped by
+    (Z, budget), so per-batch launches read contiguous blocks; frame ids run in
+    that order (channel counter and Algorithm 4 keys)."""
+    import torch
+    from paper_2102_11089_gb300 import workloads as wl
+    design = wl.bg2_like(3)
+    rng = np.random.default_rng(seed)
+    zi = rng.integers(0, len(QUEUE_ZS), frames)
+    ebn0 = rng.uniform(0.5, 3.0, frames).astype(np.float32)
+    bud = rng.integers(2, 21, frames)
+    order = np.lexsort((bud, zi))
+    zi, ebn0, bud = zi[order], ebn0[order], bud[order]
+    codes = [L.Code.from_protograph(design.shifts(Z), Z, design.info_cols * Z, design.punct_cols)
+             for Z in QUEUE_ZS]
+    Ns = np.array([c.N for c in codes])
+    Es = np.array([c.E for c in codes])
+    Ks = np.array([c.K for c in codes])
+    n_of = Ns[zi]
+    off = np.concatenate([[0], np.cumsum(n_of)[:-1]]).astype(np.int64)
+    total = int(n_of.sum())
+    dt = torch.int8 if arith == "int6" else torch.float32
+    llr = torch.empty(total, dtype=dt, device=device)
+    groups = []  # (code index, budget, first frame, count, offset)
+    for ci, c in enumerate(codes):
+        idx = np.nonzero(zi == ci)[0]
+        if len(idx) == 0:
+            continue
+        f0, B = int(idx[0]), len(idx)
+        eb = torch.from_numpy(ebn0[idx]).to(device)
+        lam, q = L.awgn_llr(c, eb, seed=2021, frame_offset=f0, quantize=arith == "int6")
+        x = q if arith == "int6" else lam
+        llr[off[f0]:off[f0] + B * c.N].copy_(x.reshape(-1))
+        for b in np.unique(bud[idx]):
+            sub = idx[bud[idx] == b]
+            groups.append((ci, int(b) * c.E, int(sub[0]), len(sub), int(off[sub[0]])))
+    budget = bud * Es[zi]
+    return dict(codes=codes, zi=zi, budget=budget, off=off, total=total, llr=llr, groups=groups,
+                info_bits=int(Ks[zi].sum()), Es=Es, frames=frames)
+
+
+def run_queue_mixed(args, L, device, frames=None, reps=2):
+    """Persistent work queue (one launch, items in decreasing-cost order, launch
+    shape from the autotuner) against per-batch launches of the same frames:
+    ldpc_decode per (Z, budget) group, and the queue kernel in static mode per
+    Z group.  Every form computes the same results (checked)."""
+    import tempfile
+    import torch
+    from paper_2102_11089_gb300 import autotune as at
+    frames = frames or args.queue_frames
+    arith = "fp32"
+    w = mixed_bg2(L, device, frames, arith)
+    codes, zi, F = w["codes"], w["zi"], frames
+    p = L.make_params("me-lmd-cirbp", arith, gamma=0.1, n_p=args.n_p, n_g=args.n_g, check_interval=1, seed=1234)
+    cost = w["budget"].astype(np.float64)
+    lpt = np.argsort(-cost, kind="stable")
+    items = L.make_items(zi[lpt], w["off"][lpt], w["off"][lpt], w["budget"][lpt], lpt, device=device)
+    hard = torch.empty(w["total"], dtype=torch.uint8, device=device)
+    upd = torch.empty(F, dtype=torch.int64, device=device)
+    conv = torch.empty(F, dtype=torch.uint8, device=device)
+
+    def ev_time(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.min(ts))
+
+    # autotune the queue launch on a calibration queue (the costliest quarter of the items)
+    nc = max(1, F // 4)
+    cal = L.make_items(zi[lpt[:nc]], w["off"][lpt[:nc]], w["off"][lpt[:nc]], w["budget"][lpt[:nc]],
+                       lpt[:nc], device=device)
+    with tempfile.TemporaryDirectory() as d:
+        cache = at.TuneCache(os.path.join(d, "tune.json"))
+        tune = at.tune_queue(codes, cal, nc, w["llr"], p, hard=hard, updates=upd, converged=conv,
+                             cache=cache, repeats=1)
+        tune_ms = json.load(open(cache.path))
+    tune_ms = next(iter(tune_ms.values()))["ms"]
+    p.tune = tune
+
+    def persistent():
+        L.decode_queue(codes, items, F, w["llr"], p, hard=hard, updates=upd, converged=conv,
+                       mode=L.QUEUE_PERSISTENT)
+
+    ms_q = ev_time(persistent, reps)
+    inv = torch.from_numpy(np.argsort(lpt)).to(device)
+    upd_q, conv_q = upd[inv].clone(), conv[inv].clone()  # item order -> frame id
+
+    # per-batch launches: ldpc_decode per (Z, budget) group
+    p_b = L.make_params("me-lmd-cirbp", arith, gamma=0.1, n_p=args.n_p, n_g=args.n_g, check_interval=1,
+                        seed=1234)
+    hard_b = torch.empty_like(hard)
+    upd_b = torch.empty(F, dtype=torch.int64, device=device)
+    conv_b = torch.empty(F, dtype=torch.uint8, device=device)
+    views = []
+    for ci, budget, f0, B, o in w["groups"]:
+        c = codes[ci]
+        x = w["llr"][o:o + B * c.N].view(B, c.N)
+        out = dict(hard=hard_b[o:o + B * c.N].view(B, c.N), updates=upd_b[f0:f0 + B],
+                   converged=conv_b[f0:f0 + B])
+        pg = L.make_params("me-lmd-cirbp", arith, gamma=0.1, n_p=args.n_p, n_g=args.n_g,
+                           check_interval=1, seed=1234, max_updates=budget, frame_offset=f0)
+        views.append((c, x, pg, out))
+
+    def per_batch():
+        for c, x, pg, out in views:
+            L.decode(c, x, pg, out=out)
+
+    ms_b = ev_time(per_batch, reps)
+
+    # queue kernel in static mode (one CTA per item), one launch per Z group
+    zitems = []
+    for ci in range(len(codes)):
+        idx = np.nonzero(zi == ci)[0]
+        if len(idx):
+            zitems.append((L.make_items(zi[idx], w["off"][idx], w["off"][idx], w["budget"][idx], idx,
+                                        device=device), len(idx)))
+    hard_s = torch.empty_like(hard)
+    upd_s = torch.empty(F, dtype=torch.int64, device=device)
+    conv_s = torch.empty(F, dtype=torch.uint8, device=device)
+
+    def static_per_z():
+        pos = 0
+        for it, n in zitems:
+            L.decode_queue(codes, it, n, w["llr"], p_b, hard=hard_s, updates=upd_s[pos:pos + n],
+                           converged=conv_s[pos:pos + n], mode=L.QUEUE_STATIC)
+            pos += n
+
+    ms_s = ev_time(static_per_z, reps)
+    torch.cuda.synchronize()
+    L.sync()
+    same = bool(torch.equal(hard, hard_b) and torch.equal(upd_q, upd_b) and torch.equal(conv_q, conv_b)
+                and torch.equal(hard, hard_s) and torch.equal(upd_s, upd_b) and torch.equal(conv_s, conv_b))
+    # frame errors: any decided bit of a frame set (all-zero codeword)
+    errs = 0
+    hb = hard.cpu().numpy()
+    for f in range(F):
+        n = codes[zi[f]].N
+        o = w["off"][f]
+        errs += int(hb[o:o + n].any())
+    gbit = lambda ms: w["info_bits"] / (ms * 1e-3) / 1e9  # noqa: E731
+    return {"workload": "bg2-like 42x52, Z~U{16..384}, Eb/N0~U[0.5,3] dB, budget~U{2..20}E per frame",
+            "frames": F, "schedule": "me-lmd-cirbp", "arith": arith, "n_p": args.n_p,
+            "fer": errs / F, "mean_updates_per_frame": float(upd_b.float().mean().item()),
+            "identical_results": same,
+            "persistent": {"ms": ms_q, "gbit_s": gbit(ms_q), "launches": 1, "tune": tune,
+                           "tune_shape": at.describe(tune), "tune_search_ms": tune_ms,
+                           "order": "decreasing budget"},
+            "per_batch_decode": {"ms": ms_b, "gbit_s": gbit(ms_b), "launches": len(views),
+                                 "grouping": "(Z, budget)"},
+            "static_queue_per_z": {"ms": ms_s, "gbit_s": gbit(ms_s), "launches": len(zitems)},
+            "speedup_vs_per_batch": ms_b / ms_q, "speedup_vs_static_per_z": ms_s / ms_q}
 
 
 def run_decode_only(args):
@@ -493,6 +664,13 @@ def run_decode_only(args):
 
 def main():
     args = parse()
+    if args.queue_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2102_11089_gb300 as L
+        print(json.dumps(run_queue_mixed(args, L, torch.device("cuda", 0), reps=args.reps)))
+        return
     if args.decode_only:
         run_decode_only(args)
         return

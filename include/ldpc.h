@@ -89,7 +89,8 @@ typedef struct {
     int32_t schedule;       /* LDPC_FLOODING .. LDPC_ME_LMD_CIRBP                 */
     int32_t arith;          /* LDPC_FP32_SUMPRODUCT or LDPC_INT6_MINSUM           */
     double gamma;           /* CIRBP threshold on D (Alg. 1 line 5), in [0, 1)    */
-    int32_t n_p;            /* multi-edge: VNs updated per step (N_P, Sec. 6)     */
+    int32_t n_p;            /* multi-edge: VNs updated per step (N_P, Sec. 6),
+                               1..384                                             */
     int32_t n_g;            /* multi-edge: CI groups of Algorithm 4 (N_G)         */
     int64_t max_updates;    /* budget in committed C2V messages (E = 1 iteration,
                                Sec. 2.A); flooding uses whole iterations only     */
@@ -104,11 +105,14 @@ typedef struct {
     uint64_t frame_offset;  /* global index of frame 0 of this batch (Philox ctr)  */
     int32_t form;           /* LDPC_FORM_*                                        */
     int32_t tune;           /* launch-shape hints (0 = library defaults), set by the
-                               project's autotuner: bits 0-1 CTA size of CTA-per-frame
-                               kernels (1 = 256, 2 = 512 threads); bits 4-5 frame state
-                               of the queue form (1 = shared memory for codes whose
-                               state fits two CTAs per SM, 2 = fits one CTA per SM,
-                               3 = global memory only); other bits must be 0        */
+                               project's autotuner (paper_2102_11089_gb300.autotune):
+                               bits 0-1 CTA size of the multi-edge kernels (1 = 256,
+                               2 = 512 threads); bits 2-3 frames (warps) per CTA of
+                               the single-edge kernels in shared memory (1 = 2,
+                               2 = 4, 3 = 8, fewer when they do not fit); bits 4-5
+                               frame state of the queue form (0 = shared memory for
+                               codes whose state fits two CTAs per SM, 1 = three,
+                               2 = one, 3 = global memory only); other bits 0       */
 } ldpc_decode_params_t;
 
 /* One frame of the work queue of ldpc_decode_queue. */

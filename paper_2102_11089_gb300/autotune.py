@@ -1,0 +1,176 @@
+"""Launch-shape autotuner for the decode entry points.
+
+The decode kernels take launch-shape hints in ``ldpc_decode_params_t.tune``:
+CTA size of the multi-edge kernels (bits 0-1), frames per CTA of the
+single-edge kernels (bits 2-3) and, for the work-queue form, where frame state
+lives (bits 4-5: shared memory for codes that fit two, three or one CTA per
+SM, or global memory only).  None of them changes a result; they only move
+work between threads, CTAs and memories.
+
+The tuner runs a grid search over the hints that apply to a call on a
+calibration input, times each candidate with CUDA events (best of a few runs
+after one warm-up), keeps the fastest (equal times to the smaller hint) and
+caches it per (GPU, codes, parameters, entry point) in a JSON file, so a
+serving process pays the search once per configuration.  The cache file is
+``$LDPC_TUNE_CACHE`` if set, else ``~/.cache/paper_2102_11089_gb300/tune.json``.
+"""
+from __future__ import annotations
+
+import json
+import os
+import tempfile
+import threading
+
+from . import FLOODING, ME_CIRBP, ME_LMD_CIRBP, RBP, CIRBP, LMD_CIRBP  # noqa: F401
+
+CTA_256, CTA_512 = 1, 2
+PLACE_HALF, PLACE_THIRD, PLACE_FULL, PLACE_GLOBAL = 0, 1, 2, 3
+
+
+def candidates(entry: str, schedule: int) -> list[int]:
+    """Hints that can change the launch of `entry` ("decode" or "queue")."""
+    multi = schedule in (ME_CIRBP, ME_LMD_CIRBP)
+    if entry == "queue":
+        if multi:
+            return [cta | (pl << 4) for cta in (CTA_256, CTA_512)
+                    for pl in (PLACE_HALF, PLACE_THIRD, PLACE_FULL, PLACE_GLOBAL)]
+        return [pl << 4 for pl in (PLACE_HALF, PLACE_THIRD, PLACE_FULL, PLACE_GLOBAL)]
+    if entry != "decode":
+        raise ValueError(f"unknown entry point {entry!r}")
+    if multi:
+        return [CTA_256, CTA_512]
+    if schedule == FLOODING:
+        return [0]
+    return [fpc << 2 for fpc in (0, 1, 2, 3)]
+
+
+def describe(tune: int) -> dict:
+    cta = {0: "default", 1: 256, 2: 512}[tune & 3]
+    fpc = {0: "auto", 1: 2, 2: 4, 3: 8}[(tune >> 2) & 3]
+    place = {0: "smem<=1/2 SM", 1: "smem<=1/3 SM", 2: "smem<=1 SM", 3: "global"}[(tune >> 4) & 3]
+    return {"cta_threads": cta, "frames_per_cta": fpc, "queue_state": place}
+
+
+def cache_key(entry: str, device: str, codes, params) -> str:
+    """Key of one configuration: the GPU, each code's shape, and the
+    parameters that change the work (not the seed or the frame offset)."""
+    shapes = ";".join(f"{c.M}x{c.N}e{c.E}z{c.info.qc_lifting}" for c in codes)
+    p = params
+    return (f"{entry}|{device}|{shapes}|s{p.schedule}a{p.arith}np{p.n_p}ng{p.n_g}"
+            f"b{p.max_updates}ci{p.check_interval}f{p.form}")
+
+
+class TuneCache:
+    """A JSON file of {key: {"tune": int, "ms": {tune: ms}}}, written atomically."""
+
+    def __init__(self, path: str | None = None):
+        if path is None:
+            path = os.environ.get("LDPC_TUNE_CACHE") or os.path.join(
+                os.path.expanduser("~"), ".cache", "paper_2102_11089_gb300", "tune.json")
+        self.path = path
+        self._lock = threading.Lock()
+        self._data = None
+
+    def _load(self) -> dict:
+        if self._data is None:
+            try:
+                with open(self.path) as f:
+                    self._data = json.load(f)
+            except (OSError, ValueError):
+                self._data = {}
+        return self._data
+
+    def get(self, key: str):
+        with self._lock:
+            hit = self._load().get(key)
+            return None if hit is None else int(hit["tune"])
+
+    def put(self, key: str, tune: int, times: dict):
+        with self._lock:
+            data = self._load()
+            data[key] = {"tune": int(tune), "ms": {str(k): float(v) for k, v in times.items()}}
+            d = os.path.dirname(self.path)
+            if d:
+                os.makedirs(d, exist_ok=True)
+            fd, tmp = tempfile.mkstemp(dir=d or ".", prefix=".tune.")
+            with os.fdopen(fd, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+
+
+def cuda_timer(fn) -> float:
+    """Milliseconds of `fn()` on the current CUDA stream (events, synchronised)."""
+    import torch
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    fn()
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def search(run, cands, *, repeats: int = 3, timer=cuda_timer) -> tuple[int, dict]:
+    """Time `run(tune)` for every candidate (one warm-up, best of `repeats`);
+    return the fastest hint (equal times: the smaller hint) and all times."""
+    if not cands:
+        raise ValueError("no candidates")
+    times = {}
+    for t in cands:
+        run(t)  # warm-up: first-use uploads, kernel attributes
+        times[t] = min(timer(lambda t=t: run(t)) for _ in range(max(1, repeats)))
+    best = min(sorted(times), key=lambda t: times[t])
+    return best, times
+
+
+def _device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def tune_decode(code, llr, params, *, cache: TuneCache | None = None, repeats: int = 3, timer=cuda_timer,
+                device: str | None = None) -> int:
+    """Best `tune` for ldpc_decode of `llr` (a calibration batch) with
+    `params`; sets params.tune and returns it."""
+    from . import decode
+    cache = cache if cache is not None else TuneCache()
+    key = cache_key("decode", device or _device_name(), [code], params)
+    hit = cache.get(key)
+    if hit is None:
+        state = {}
+        base = params.tune
+
+        def run(t):
+            params.tune = t
+            state["out"] = decode(code, llr, params, out=state.get("out"))
+
+        hit, times = search(run, candidates("decode", params.schedule), repeats=repeats, timer=timer)
+        params.tune = base
+        cache.put(key, hit, times)
+    params.tune = hit
+    return hit
+
+
+def tune_queue(codes, items, n_items: int, llr, params, *, hard=None, updates=None, converged=None,
+               cache: TuneCache | None = None, repeats: int = 3, timer=cuda_timer, device: str | None = None,
+               mode=None) -> int:
+    """Best `tune` for ldpc_decode_queue over a calibration queue; sets
+    params.tune and returns it."""
+    from . import QUEUE_PERSISTENT, decode_queue
+    mode = QUEUE_PERSISTENT if mode is None else mode
+    cache = cache if cache is not None else TuneCache()
+    key = cache_key(f"queue{mode}", device or _device_name(), codes, params)
+    hit = cache.get(key)
+    if hit is None:
+        base = params.tune
+
+        def run(t):
+            params.tune = t
+            decode_queue(codes, items, n_items, llr, params, hard=hard, updates=updates, converged=converged,
+                         mode=mode)
+
+        hit, times = search(run, candidates("queue", params.schedule), repeats=repeats, timer=timer)
+        params.tune = base
+        cache.put(key, hit, times)
+    params.tune = hit
+    return hit

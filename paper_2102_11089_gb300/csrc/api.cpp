@@ -492,9 +492,9 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   if (!(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
   if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
-  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 1024))
-    return fail(LDPC_ERR_INVALID_ARG, "n_p > 0 and 0 < n_g <= 1024 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
+  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 1024))
+    return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 1024 required");
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x3f) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
@@ -587,6 +587,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   } else if (p->schedule >= LDPC_RBP && p->schedule <= LDPC_LMD_CIRBP) {
     // frames per CTA: fill about half the opt-in shared memory so two CTAs share an SM
     int fpc = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t)std::max(0, optin / 2 - gsm) / per));
+    if ((p->tune >> 2) & 3) fpc = 1 << ((p->tune >> 2) & 3);  // 2, 4 or 8 frames by request
     while (fpc > 1 && (int)(fpc * per) + gsm > optin) --fpc;
     if ((int64_t)fpc > batch) fpc = (int)batch;
     a.frames_per_cta = fpc;
@@ -619,10 +620,10 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
   if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
   if (p->check_interval < 0 || !(p->gamma >= 0.0 && p->gamma <= 1.0) || !(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f) ||
-      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
+      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0x3f) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad parameters");
   const bool me = p->schedule != LDPC_LMD_CIRBP;
-  if (me && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 255)) return fail(LDPC_ERR_INVALID_ARG, "n_p, n_g");
+  if (me && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255)) return fail(LDPC_ERR_INVALID_ARG, "n_p, n_g");
   if (n_items == 0) return LDPC_OK;
   if (!items || !llr) return fail(LDPC_ERR_INVALID_ARG, "items and llr are required");
   int dev = 0;
@@ -656,9 +657,10 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
   const size_t fixed = graph_bytes + small_bytes + (me ? 1024 : 0);
   if ((int64_t)fixed > optin) return fail(LDPC_ERR_UNSUPPORTED, "working set exceeds shared memory");
   // frame state in shared memory for codes up to a size: two CTAs per SM by
-  // default (or one, or none, by tune bits 4-5); larger codes use global slots
+  // default (three, one or none by tune bits 4-5); larger codes use global slots
   const int placement = (p->tune >> 4) & 3;
-  const size_t budget = placement == 3 ? 0 : (placement == 2 ? (size_t)optin - fixed : (size_t)optin / 2 - fixed);
+  const int64_t share = placement == 3 ? 0 : (placement == 2 ? optin : (placement == 1 ? optin / 3 - 1024 : optin / 2 - 1024));
+  const size_t budget = share > (int64_t)fixed ? (size_t)(share - (int64_t)fixed) : 0;
   size_t sstate = 0;
   for (size_t b : bigs)
     if (b <= budget) sstate = std::max(sstate, b);
@@ -666,8 +668,12 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
   const size_t smem = fixed + sstate;
   int grid;
   if (mode == LDPC_QUEUE_PERSISTENT) {
-    int per_sm = me ? std::max(1, (int)std::min<size_t>(2048 / threads, (size_t)228 * 1024 / (smem + 1024)))
-                    : std::max(1, (int)std::min<size_t>(32, (size_t)228 * 1024 / (smem + 1024)));
+    // one CTA per resident slot: the occupancy of the kernel actually launched
+    int per_sm = 0;
+    const cudaError_t e = me ? ldpc::me_queue_blocks_per_sm(arith, p->schedule, threads, smem, &per_sm)
+           : ldpc::se_queue_blocks_per_sm(arith, smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (per_sm < 1) return fail(LDPC_ERR_UNSUPPORTED, "queue kernel does not fit an SM");
     grid = (int)std::min<int64_t>(n_items, (int64_t)sms * per_sm);
   } else {
     if (n_items > 0x7fffffff) return fail(LDPC_ERR_UNSUPPORTED, "too many items for one launch");

@@ -862,6 +862,26 @@ cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int thread
   return big ? launch_me_queue_tpb<kINT6, kMECIRBP, 512>(q, grid, smem, s) : launch_me_queue_tpb<kINT6, kMECIRBP, 256>(q, grid, smem, s);
 }
 
+namespace {
+template <int A, int S, int TPB>
+cudaError_t me_queue_occ(size_t smem, int* out) {
+  auto k = me_queue_kernel<A, S, TPB>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, TPB, smem);
+}
+}  // namespace
+
+cudaError_t me_queue_blocks_per_sm(int arith, int sched, int threads, size_t smem, int* out) {
+  const bool lmd = sched == kMELMD, big = threads == 512;
+  if (arith == kFP32) {
+    if (lmd) return big ? me_queue_occ<kFP32, kMELMD, 512>(smem, out) : me_queue_occ<kFP32, kMELMD, 256>(smem, out);
+    return big ? me_queue_occ<kFP32, kMECIRBP, 512>(smem, out) : me_queue_occ<kFP32, kMECIRBP, 256>(smem, out);
+  }
+  if (lmd) return big ? me_queue_occ<kINT6, kMELMD, 512>(smem, out) : me_queue_occ<kINT6, kMELMD, 256>(smem, out);
+  return big ? me_queue_occ<kINT6, kMECIRBP, 512>(smem, out) : me_queue_occ<kINT6, kMECIRBP, 256>(smem, out);
+}
+
 size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g) {
   (void)sched;
   (void)n_p;

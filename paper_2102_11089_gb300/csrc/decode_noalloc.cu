@@ -80,9 +80,9 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   if (!(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
   if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
-  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_g <= 0 || p->n_g > 255))
-    return fail(LDPC_ERR_INVALID_ARG, "n_p > 0 and 0 < n_g <= 255 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x33) != 0 || (p->tune & 3) == 3)
+  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255))
+    return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 255 required");
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x3f) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");

@@ -454,6 +454,20 @@ cudaError_t launch_sched(const DecodeArgs& a, int sched, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+template <int A>
+cudaError_t se_queue_occ(size_t smem, int* out) {
+  auto k = se_queue_kernel<A, kLMD>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, 32, smem);
+}
+}  // namespace
+
+cudaError_t se_queue_blocks_per_sm(int arith, size_t smem, int* out) {
+  return arith == kFP32 ? se_queue_occ<kFP32>(smem, out) : se_queue_occ<kINT6>(smem, out);
+}
+
 cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem, cudaStream_t s) {
   if (q.n_items == 0) return cudaSuccess;
   return arith == kFP32 ? launch_se_queue_t<kFP32, kLMD>(q, grid, smem, s) : launch_se_queue_t<kINT6, kLMD>(q, grid, smem, s);

@@ -176,6 +176,9 @@ struct QueueArgs {
 cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int threads, int grid, size_t smem,
                             cudaStream_t s);
 cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem, cudaStream_t s);
+// resident CTAs per SM of the queue kernels with `smem` bytes of dynamic shared memory
+cudaError_t me_queue_blocks_per_sm(int arith, int sched, int threads, size_t smem, int* out);
+cudaError_t se_queue_blocks_per_sm(int arith, size_t smem, int* out);
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
 cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s);
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s);

@@ -135,9 +135,10 @@ def test_decode_validation_needs_no_gpu(lib):
         setattr(q, field, val)
         assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
                                null) == -1, field
-    q = L.make_params("me-cirbp", max_updates=10, n_p=0)
-    assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
-                           null) == -1
+    for n_p in (0, 385):
+        q = L.make_params("me-cirbp", max_updates=10, n_p=n_p)
+        assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
+                               null) == -1
     q = L.make_params("rbp", "int6", max_updates=10, q_step=0.0)
     assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
                            null) == -1

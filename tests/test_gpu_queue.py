@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import paper_2102_11089_gb300 as L
+from paper_2102_11089_gb300 import autotune as at
 from paper_2102_11089_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -128,3 +129,49 @@ def test_queue_flags_item_with_bad_code_index():
     assert conv[1].item() == 2 and upd[1].item() == 0
     assert conv[0].item() in (0, 1) and upd[0].item() > 0
     L.sync()  # the status word was cleared
+
+
+@pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "lmd-cirbp"])
+def test_queue_results_do_not_depend_on_tune(schedule, tmp_path):
+    codes, groups, rows, items, llr, total = _mixed_queue("int6", Zs=(16, 64, 128), per=(4, 3, 2))
+    p = L.make_params(schedule, "int6", n_p=32, n_g=16, seed=9)
+    n = len(rows)
+    ref = None
+    for t in at.candidates("queue", p.schedule):
+        p.tune = t
+        hard = torch.full((total,), 7, dtype=torch.uint8, device="cuda")
+        upd = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        conv = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
+        L.decode_queue(codes, items, n, llr, p, hard=hard, updates=upd, converged=conv)
+        torch.cuda.synchronize()
+        got = (hard.cpu().numpy(), upd.cpu().numpy(), conv.cpu().numpy())
+        if ref is None:
+            ref = got
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), t
+    p.tune = 0
+    best = at.tune_queue(codes, items, n, llr, p, hard=hard, updates=upd, converged=conv,
+                         cache=at.TuneCache(str(tmp_path / "t.json")), repeats=1)
+    assert best in at.candidates("queue", p.schedule) and p.tune == best
+
+
+@pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "lmd-cirbp", "cirbp"])
+def test_decode_results_do_not_depend_on_tune(schedule, tmp_path):
+    d = wl.wifi_like(2, 96)
+    code = L.Code.from_protograph(d.shifts(96), 96, d.info_cols * 96, d.punct_cols)
+    q = wl.quantize_llrs(wl.seeded_llrs(code.N, 40, wl.sigma2_from_ebn0(1.75, 0.5), 12), 0.5)
+    x = torch.from_numpy(q).cuda()
+    p = L.make_params(schedule, "int6", n_p=64, n_g=16, max_updates=2 * code.E, seed=3)
+    ref = None
+    for t in at.candidates("decode", p.schedule):
+        p.tune = t
+        out = L.decode(code, x, p, want_llr=True)
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        if ref is None:
+            ref = got
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), (t, k)
+    p.tune = 0
+    best = at.tune_decode(code, x, p, cache=at.TuneCache(str(tmp_path / "t.json")), repeats=1)
+    assert best in at.candidates("decode", p.schedule)
