@@ -53,6 +53,10 @@ def parse():
                     help="frames of the mixed-lifting BG2-shaped queue comparison (extras)")
     ap.add_argument("--queue-only", action="store_true",
                     help="run only the mixed-lifting queue comparison and print its JSON")
+    ap.add_argument("--large-frames", type=int, default=304,
+                    help="frames per point of the 26,112-bit BG1-shaped comparison (extras)")
+    ap.add_argument("--large-only", action="store_true",
+                    help="run only the BG1-shaped cluster / global-memory comparison and print its JSON")
     return ap.parse_args()
 
 
@@ -471,6 +475,8 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
                                     "gbit_s": B3 * code.K / (ms_se * 1e-3) / 1e9}
     if args.queue_frames > 0:
         res["queue_mixed_bg2"] = run_queue_mixed(args, L, device)
+    if args.large_frames > 0:
+        res["large_bg1_z384"] = run_large_bg1(args, L, device)
     return res
 
 
@@ -639,6 +645,42 @@ def run_queue_mixed(args, L, device, frames=None, reps=2):
             "speedup_vs_per_batch": ms_b / ms_q, "speedup_vs_static_per_z": ms_s / ms_q}
 
 
+def run_large_bg1(args, L, device, frames=None, reps=2, points=None):
+    """The BG1-shaped code (46x68 protograph, Z=384: n=26,112, about 120k edges),
+    ME-LMD-CIRBP at Eb/N0 = 1.2 dB with budget 5E: frame state spread over a
+    thread-block cluster's shared memory against global-memory slots, FP32 and
+    6-bit, N_P = 64 and 256.  Both forms give identical results (checked)."""
+    import torch
+    from paper_2102_11089_gb300 import workloads as wl
+    frames = frames or args.large_frames
+    d = wl.bg1_like(5)
+    code = L.Code.from_protograph(d.shifts(384), 384, d.info_cols * 384, d.punct_cols)
+    eb = torch.full((frames,), 1.2, dtype=torch.float32, device=device)
+    res = {"workload": "bg1-like 46x68, Z=384, n=26112, Eb/N0 1.2 dB, budget 5E", "frames": frames,
+           "n": code.N, "edges": code.E, "k": code.K, "points": []}
+    for arith, n_p in (points or [("fp32", 64), ("fp32", 256), ("int6", 256)]):
+        lam, q = L.awgn_llr(code, eb, seed=2021, frame_offset=0, quantize=arith == "int6")
+        x = q if arith == "int6" else lam
+        row = {"arith": arith, "n_p": n_p}
+        outs = {}
+        for name, form in (("cluster", L.FORM_CLUSTER), ("global", L.FORM_GLOBAL)):
+            p = L.make_params("me-lmd-cirbp", arith, gamma=0.1, n_p=n_p, n_g=16, max_updates=5 * code.E,
+                              check_interval=1, seed=1234, form=form)
+            try:
+                ms, o = time_decode(L, code, x, p, reps=reps)
+            except L.LdpcError as e:
+                row[name] = {"unavailable": str(e)}
+                continue
+            outs[name] = o
+            row[name] = {"ms": ms, "gbit_s": frames * code.K / (ms * 1e-3) / 1e9, "fer": fer_of(o),
+                         "mean_updates": float(o["updates"].float().mean().item())}
+        if len(outs) == 2:
+            row["identical_results"] = all(torch.equal(outs["cluster"][k], outs["global"][k]) for k in outs["global"])
+            row["speedup_cluster_vs_global"] = row["global"]["ms"] / row["cluster"]["ms"]
+        res["points"].append(row)
+    return res
+
+
 def run_decode_only(args):
     import torch
     import __graft_entry__
@@ -670,6 +712,13 @@ def main():
         __graft_entry__.build()
         import paper_2102_11089_gb300 as L
         print(json.dumps(run_queue_mixed(args, L, torch.device("cuda", 0), reps=args.reps)))
+        return
+    if args.large_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2102_11089_gb300 as L
+        print(json.dumps(run_large_bg1(args, L, torch.device("cuda", 0), reps=args.reps)))
         return
     if args.decode_only:
         run_decode_only(args)

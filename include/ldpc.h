@@ -64,6 +64,8 @@ typedef int32_t ldpc_status_t;
 #define LDPC_FORM_AUTO 0   /* pick by code size                                   */
 #define LDPC_FORM_SMEM 1   /* frame state in shared memory (warp or CTA / frame)  */
 #define LDPC_FORM_GLOBAL 2 /* frame state in device global memory (large codes)   */
+#define LDPC_FORM_CLUSTER 3 /* multi-edge: frame state spread over the shared memory
+                             of a thread-block cluster (large codes)          */
 
 /* per-frame flag bits written to `converged` */
 #define LDPC_FRAME_CONVERGED 1u /* final hard decision satisfies every check      */
@@ -112,7 +114,9 @@ typedef struct {
                                2 = 4, 3 = 8, fewer when they do not fit); bits 4-5
                                frame state of the queue form (0 = shared memory for
                                codes whose state fits two CTAs per SM, 1 = three,
-                               2 = one, 3 = global memory only); other bits 0       */
+                               2 = one, 3 = global memory only); bits 6-7 CTAs per
+                               cluster of the cluster form (0 = smallest that fits,
+                               1 = 4, 2 = 8, 3 = 16); other bits 0                  */
 } ldpc_decode_params_t;
 
 /* One frame of the work queue of ldpc_decode_queue. */
@@ -196,7 +200,13 @@ ldpc_status_t ldpc_awgn_llr(const ldpc_code_t *code, const float *ebn0_db, int64
  * llr_out   : device float[batch][n_vars] or NULL: final total LLR L_n, eq. (3)
  *             (INT6: the integer value)
  * Stops at a zero syndrome (checked per check_interval) or at the budget.
- * Errors: INVALID_ARG, UNSUPPORTED (no execution form fits), CUDA, NOMEM. */
+ * Execution form (params->form = LDPC_FORM_AUTO): frame state in shared
+ * memory when it fits one CTA; else, for the multi-edge schedules, spread
+ * over the shared memory of a thread-block cluster (the smallest of 2, 4, 8
+ * or 16 CTAs that holds it and can be resident); else global memory.  The
+ * form never changes a result.
+ * Errors: INVALID_ARG, UNSUPPORTED (no execution form fits; LDPC_FORM_CLUSTER
+ * with a single-edge or flooding schedule), CUDA, NOMEM. */
 ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batch,
                           const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
                           uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);

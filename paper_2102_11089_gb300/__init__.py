@@ -24,7 +24,7 @@ FLOODING, RBP, CIRBP, LMD_CIRBP, ME_CIRBP, ME_LMD_CIRBP = range(6)
 SCHEDULES = {"flooding": FLOODING, "rbp": RBP, "cirbp": CIRBP, "lmd-cirbp": LMD_CIRBP,
              "me-cirbp": ME_CIRBP, "me-lmd-cirbp": ME_LMD_CIRBP}
 FP32_SUMPRODUCT, INT6_MINSUM = 0, 1
-FORM_AUTO, FORM_SMEM, FORM_GLOBAL = 0, 1, 2
+FORM_AUTO, FORM_SMEM, FORM_GLOBAL, FORM_CLUSTER = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "_lib", "libldpc_gb300.so")

@@ -494,8 +494,10 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 1024))
     return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 1024 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_GLOBAL || (p->tune & ~0x3f) != 0 || (p->tune & 3) == 3)
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0xff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
+  if (p->form == LDPC_FORM_CLUSTER && p->schedule < LDPC_ME_CIRBP)
+    return fail(LDPC_ERR_UNSUPPORTED, "the cluster form runs the multi-edge schedules");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
 
@@ -563,6 +565,26 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   }
   const bool fits = (int64_t)per + (int64_t)cta_fixed + gsm <= optin;
   if (p->form == LDPC_FORM_SMEM && !fits) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+  // Cluster form (multi-edge, on request or for frames too large for one CTA):
+  // the smallest cluster (or the requested size) whose shared memory holds the
+  // frame state and that can be resident; else the global-memory form.
+  if (p->schedule >= LDPC_ME_CIRBP && (p->form == LDPC_FORM_CLUSTER || (p->form == LDPC_FORM_AUTO && !fits))) {
+    const int req = (p->tune >> 6) & 3;
+    const int threads = (p->tune & 3) == 1 ? 256 : 512;
+    const int64_t avail = (int64_t)optin - gsm - 1024;
+    for (int cs = req ? (2 << req) : 2; cs <= (req ? (2 << req) : 16); cs *= 2) {
+      if (!ldpc::me_cluster_plan(arith, *g, p->n_p, p->n_g, cs, avail, &a.cl)) continue;
+      a.cta_threads = threads;
+      e = ldpc::launch_me_cluster(a, arith, p->schedule, threads, s);
+      if (e == cudaSuccess) return LDPC_OK;
+      a.cl.cs = 0;
+      if (e != cudaErrorInvalidConfiguration && e != cudaErrorInvalidValue && e != cudaErrorNotSupported &&
+          e != cudaErrorInvalidClusterSize)
+        return cuda_fail(e, "cluster decode launch");
+      (void)cudaGetLastError();  // this size cannot be resident: try the next
+    }
+    if (p->form == LDPC_FORM_CLUSTER) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds a resident cluster");
+  }
   if ((int64_t)cta_fixed + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "working set exceeds shared memory");
   const bool global_form = p->form == LDPC_FORM_GLOBAL || !fits;
   void* scratch = nullptr;
@@ -620,7 +642,7 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
   if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
   if (p->check_interval < 0 || !(p->gamma >= 0.0 && p->gamma <= 1.0) || !(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f) ||
-      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0x3f) != 0 || (p->tune & 3) == 3)
+      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0xff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad parameters");
   const bool me = p->schedule != LDPC_LMD_CIRBP;
   if (me && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255)) return fail(LDPC_ERR_INVALID_ARG, "n_p, n_g");

@@ -27,13 +27,77 @@
 // n mod 4 of Philox4x32-10 with counter (n/4, step, frame), key = seed; equal
 // keys to the lower index): members with key <= T are gathered (T bisected
 // until between `need` and kCap of them), then ranked exactly.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "device_math.cuh"
 
 namespace ldpc {
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int kCap = 512;  // candidate list of the random fill
+
+// Array views of the frame state.  LArr: a plain array (this CTA's shared
+// memory, or a global-memory slot).  DArr: an array spread over the shared
+// memory of the CTAs of a thread-block cluster: element i lives in rank
+// rank0 + (i >> shift) at the same offset in every rank, reached through
+// distributed shared memory.
+template <class T>
+struct LArr {
+  T* p;
+  __device__ __forceinline__ T& operator[](int i) const { return p[i]; }
+};
+template <class T>
+struct DArr {
+  T* p;  // this CTA's address of the array's chunk
+  int shift, rank0;
+  __device__ __forceinline__ T& operator[](int i) const {
+    return *cg::this_cluster().map_shared_rank(p + (i & ((1 << shift) - 1)), (unsigned)(rank0 + (i >> shift)));
+  }
+};
+
+// Thread group decoding one frame: a CTA, or all CTAs of a cluster.  tid/nt
+// number the group's threads; sync() is the group barrier (with the memory
+// ordering of __syncthreads / barrier.cluster); sync_or() a barrier that ORs
+// a flag over the group.
+struct CtaX {
+  template <class T>
+  using Arr = LArr<T>;
+  int tid, nt;
+  __device__ __forceinline__ CtaX() : tid((int)threadIdx.x), nt((int)blockDim.x) {}
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ int sync_or(int v, int*) const { return __syncthreads_or(v); }
+};
+struct ClusterX {
+  template <class T>
+  using Arr = DArr<T>;
+  int tid, nt;
+  __device__ __forceinline__ ClusterX() {
+    const cg::cluster_group c = cg::this_cluster();
+    tid = (int)(c.block_rank() * blockDim.x + threadIdx.x);
+    nt = (int)(c.num_blocks() * blockDim.x);
+  }
+  // release/acquire cluster barrier; the "memory" clobber also keeps the
+  // compiler from moving shared-memory accesses across it
+  __device__ __forceinline__ void sync() const {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+  // `flag` (one int of the cluster, zero on entry) is reset by thread 0 after use
+  __device__ __forceinline__ int sync_or(int v, int* flag) const {
+    if (__syncthreads_or(v) && threadIdx.x == 0) atomicOr(flag, 1);
+    sync();
+    const int r = *(volatile int*)flag;
+    sync();
+    if (tid == 0) *flag = 0;
+    return r;
+  }
+};
 
 // Big per-frame arrays (shared memory, or a global-memory slot for large codes)
 struct MEBig {
@@ -95,34 +159,37 @@ struct MEMisc {
   int ncand;
   uint32_t thr, lo, hi;
   int done, hi_set;
+  int orflag;  // cluster form: OR of the bad-input flags
 };
 
-template <int A>
+template <int A, class X>
 struct MEState {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
-  M_* C;
-  M_* P;
-  L_* lam;
-  L_* L;
-  D_* D;
-  int32_t* Lt;   // sum over the edges of each VN of L~^C, exact integer (see top)
-  uint8_t* grp;
-  uint32_t* par;
-  int32_t* sel;
-  int32_t* est;
-  unsigned long long* best;
-  int32_t* excl;   // P' of ME-LMD-CIRBP (excluded from Algorithm 4's top-up)
-  int2* cnl;       // (check, owner k) of every affected check
-  int32_t* cul;     // distinct affected checks
-  unsigned long long* cand;  // aliases cnl
-  uint32_t* cbits;   // checks already listed this step
-  int32_t* cnt;      // |G_i| over all VNs, kept up to date with grp
-  int32_t* cntS;     // per-group count of the VNs excluded from Algorithm 4's search set
-  uint32_t* bits;    // selection bitmap over VNs
-  uint32_t* touched; // VNs whose D was rewritten in this step
-  int32_t* lbase;    // compaction: first selection slot of each lane's word range
+  template <class T>
+  using Arr = typename X::template Arr<T>;
+  Arr<M_> C;
+  Arr<M_> P;
+  Arr<L_> lam;
+  Arr<L_> L;
+  Arr<D_> D;
+  Arr<int32_t> Lt;   // sum over the edges of each VN of L~^C, exact integer (see top)
+  Arr<uint8_t> grp;
+  Arr<uint32_t> par;
+  Arr<int32_t> sel;
+  Arr<int32_t> est;
+  Arr<unsigned long long> best;
+  Arr<int32_t> excl;   // P' of ME-LMD-CIRBP (excluded from Algorithm 4's top-up)
+  Arr<int2> cnl;       // (check, owner k) of every affected check
+  Arr<unsigned long long> cand;  // aliases cnl
+  Arr<int32_t> cul;    // distinct affected checks
+  Arr<uint32_t> cbits;   // checks already listed this step
+  Arr<int32_t> cnt;      // |G_i| over all VNs, kept up to date with grp
+  Arr<int32_t> cntS;     // per-group count of the VNs excluded from Algorithm 4's search set
+  Arr<uint32_t> bits;    // selection bitmap over VNs
+  Arr<uint32_t> touched; // VNs whose D was rewritten in this step
+  Arr<int32_t> lbase;    // compaction: first selection slot of each lane's word range
   MEMisc* misc;
   const int16_t* tab;
   float fx, ifx;     // FP32 fixed point: 2^k and 2^-k
@@ -144,14 +211,22 @@ __device__ __forceinline__ void philox4(uint32_t c[4], uint64_t seed) {
   }
 }
 
-__device__ __forceinline__ float ci_me(const MEState<kFP32>&, float a, float b) { return ci_fp(a, b); }
-__device__ __forceinline__ uint16_t ci_me(const MEState<kINT6>& s, int a, int b) { return ci_int(a, b, s.tab); }
+template <class X>
+__device__ __forceinline__ float ci_me(const MEState<kFP32, X>&, float a, float b) { return ci_fp(a, b); }
+template <class X>
+__device__ __forceinline__ uint16_t ci_me(const MEState<kINT6, X>& s, int a, int b) { return ci_int(a, b, s.tab); }
 
 // message -> exact integer term of the L~ sum, and the sum -> L~ contribution
-__device__ __forceinline__ int fix_msg(const MEState<kFP32>& s, float x) { return __float2int_rn(x * s.fx); }
-__device__ __forceinline__ int fix_msg(const MEState<kINT6>&, int8_t x) { return (int)x; }
-__device__ __forceinline__ float lt_total(const MEState<kFP32>& s, int n) { return s.lam[n] + (float)s.Lt[n] * s.ifx; }
-__device__ __forceinline__ int16_t lt_total(const MEState<kINT6>& s, int n) { return (int16_t)(s.lam[n] + s.Lt[n]); }
+template <class X>
+__device__ __forceinline__ int fix_msg(const MEState<kFP32, X>& s, float x) { return __float2int_rn(x * s.fx); }
+template <class X>
+__device__ __forceinline__ int fix_msg(const MEState<kINT6, X>&, int8_t x) { return (int)x; }
+template <class X>
+__device__ __forceinline__ float lt_total(const MEState<kFP32, X>& s, int n) {
+  return s.lam[n] + (float)s.Lt[n] * s.ifx;
+}
+template <class X>
+__device__ __forceinline__ int16_t lt_total(const MEState<kINT6, X>& s, int n) { return (int16_t)(s.lam[n] + s.Lt[n]); }
 
 // Algorithm 4 line 2: group i = floor(D N_G), clamped to N_G - 1
 __device__ __forceinline__ int group_of(float d, int ng) { return min((int)floorf(d * (float)ng), ng - 1); }
@@ -159,20 +234,20 @@ __device__ __forceinline__ int group_of(uint16_t d, int ng) { return min((int)((
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
-// cnt[idx] += v from the lanes of `mask` (the calling lanes; all of them must
-// call), one atomic per distinct idx.
-__device__ __forceinline__ void agg_add(int32_t* cnt, int idx, int v, unsigned mask) {
+// *at += v from the lanes of `mask` (the calling lanes; all of them must
+// call; at = &counter[idx]), one atomic per distinct idx.
+__device__ __forceinline__ void agg_add(int32_t* at, int idx, int v, unsigned mask) {
   const unsigned peers = __match_any_sync(mask, idx);
-  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[idx], v * __popc(peers));
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(at, v * __popc(peers));
 }
 
 // Algorithm 4 over S = O_N minus nexcl excluded VNs (their bits are set and
 // s.cntS counts them per group): sets the bits of the selected VNs (at most
 // np).  Group sizes come from the maintained s.cnt.  All threads call it.
-template <int A>
-__device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint32_t step, uint64_t frame,
-                     uint64_t seed) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+template <int A, class X>
+__device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, int nexcl, uint32_t step,
+                     uint64_t frame, uint64_t seed) {
+  const int tid = x.tid, nt = x.nt, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   MEMisc* ms = s.misc;
   if (warp == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S (one warp)
     // |G_i| over S = cnt[i] - cntS[i] (cntS counts the excluded VNs per group);
@@ -224,10 +299,9 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
       ms->ncand = 0;
     }
   }
-  __syncthreads();
+  x.sync();
   const int top = ms->top, fg = ms->fill_g, need = ms->need;
   const int nq = (N + 3) / 4;
-  const uint32_t* grp4 = (const uint32_t*)s.grp;
   // one pass over VN quads: line 3 selects Q(k*); lines 4-6 gather fill candidates
   // (key = word i of the Philox block of quad q)
   bool fill = need > 0;
@@ -237,7 +311,7 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
       const int q = q0 + lane;
       unsigned fm = 0;
       if (q < nq) {
-        const uint32_t g4 = grp4[q];
+        const uint32_t g4 = *(const uint32_t*)&s.grp[4 * q];
         const unsigned ex = (s.bits[q >> 3] >> ((q & 7) * 4)) & 0xfu;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -263,7 +337,7 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
         if (c && pos < kCap) s.cand[pos] = ((unsigned long long)w[i] << 32) | (unsigned)(4 * q + i);
       }
     }
-    __syncthreads();
+    x.sync();
     if (!fill) break;
     const int nc = ms->ncand;
     if (nc >= need && nc <= kCap) {
@@ -279,10 +353,10 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
           atomicOr(&s.bits[n >> 5], 1u << (n & 31));
         }
       }
-      __syncthreads();
+      x.sync();
       break;
     }
-    __syncthreads();  // every thread has read ncand
+    x.sync();  // every thread has read ncand
     if (tid == 0) {
       if (nc < need) {  // bisect the threshold upwards
         ms->lo = thr;
@@ -295,16 +369,16 @@ __device__ void alg4(const MEState<A>& s, int N, int np, int ng, int nexcl, uint
       }
       ms->ncand = 0;
     }
-    __syncthreads();
+    x.sync();
   }
 }
 
 // Compact the selection bitmap into s.sel (ascending), at most np entries; the
 // next step clears the bitmap.  Warp 0 splits the words into 32 ranges and
 // scans their counts; then every warp expands ranges, a lane per bit.
-template <int A>
-__device__ void compact_selection(int N, const MEState<A>& s, int np) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+template <int A, class X>
+__device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int np) {
+  const int lane = x.tid & 31, warp = x.tid >> 5, nw = x.nt >> 5;
   const int words = (N + 31) / 32;
   const int per = (words + 31) / 32;
   if (warp == 0) {
@@ -325,7 +399,7 @@ __device__ void compact_selection(int N, const MEState<A>& s, int np) {
       s.misc->npp = 0;
     }
   }
-  __syncthreads();
+  x.sync();
   for (int l = warp; l < 32; l += nw) {
     int pos = s.lbase[l];
     if (pos >= np) continue;
@@ -337,45 +411,56 @@ __device__ void compact_selection(int N, const MEState<A>& s, int np) {
       pos += __popc(bw);
     }
   }
-  __syncthreads();
+  x.sync();
 }
 
-// Decode one frame of code `gd`: big arrays at `big`, per-CTA working set at `small`.
-template <int A, int SCHED, class G>
-__device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& gd, const G& g, const FrameIO& io,
-                                         unsigned char* big, unsigned char* small, const int16_t* tab_int) {
+// State views of a frame in one CTA: big arrays at `big` (shared memory or a
+// global-memory slot), per-CTA working set at `small`.
+template <int A>
+__device__ __forceinline__ MEState<A, CtaX> cta_state(const GraphDesc& gd, const DecodeArgs& a, unsigned char* big,
+                                                      unsigned char* small, const int16_t* tab_int) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int N = gd.N, E = gd.E, M = gd.M;
-  const int np = a.n_p, ng = a.n_g;
-  const MEBig lb = me_big(A, M, N, E);
-  const MESmall ls = me_small(M, N, np, gd.dv_max, ng);
-  MEState<A> s;
-  s.C = (M_*)(big + lb.C);
-  s.P = (M_*)(big + lb.P);
-  s.lam = (L_*)(big + lb.lam);
-  s.L = (L_*)(big + lb.L);
-  s.D = (D_*)(big + lb.D);
-  s.Lt = (int32_t*)(big + lb.Lt);
-  s.grp = (uint8_t*)(big + lb.grp);
-  s.par = (uint32_t*)(big + lb.par);
-  s.sel = (int32_t*)(small + ls.sel);
-  s.est = (int32_t*)(small + ls.est);
-  s.best = (unsigned long long*)(small + ls.best);
-  s.excl = (int32_t*)(small + ls.excl);
-  s.cnl = (int2*)(small + ls.cnl);
-  s.cul = (int32_t*)(small + ls.cul);
-  s.cand = (unsigned long long*)(small + ls.cnl);
-  s.cbits = (uint32_t*)(small + ls.cbits);
-  s.cnt = (int32_t*)(small + ls.cnt);
-  s.cntS = (int32_t*)(small + ls.cntS);
-  s.bits = (uint32_t*)(small + ls.bits);
-  s.touched = (uint32_t*)(small + ls.touched);
-  s.lbase = (int32_t*)(small + ls.lbase);
+  const MEBig lb = me_big(A, gd.M, gd.N, gd.E);
+  const MESmall ls = me_small(gd.M, gd.N, a.n_p, gd.dv_max, a.n_g);
+  MEState<A, CtaX> s;
+  s.C.p = (M_*)(big + lb.C);
+  s.P.p = (M_*)(big + lb.P);
+  s.lam.p = (L_*)(big + lb.lam);
+  s.L.p = (L_*)(big + lb.L);
+  s.D.p = (D_*)(big + lb.D);
+  s.Lt.p = (int32_t*)(big + lb.Lt);
+  s.grp.p = (uint8_t*)(big + lb.grp);
+  s.par.p = (uint32_t*)(big + lb.par);
+  s.sel.p = (int32_t*)(small + ls.sel);
+  s.est.p = (int32_t*)(small + ls.est);
+  s.best.p = (unsigned long long*)(small + ls.best);
+  s.excl.p = (int32_t*)(small + ls.excl);
+  s.cnl.p = (int2*)(small + ls.cnl);
+  s.cul.p = (int32_t*)(small + ls.cul);
+  s.cand.p = (unsigned long long*)(small + ls.cnl);
+  s.cbits.p = (uint32_t*)(small + ls.cbits);
+  s.cnt.p = (int32_t*)(small + ls.cnt);
+  s.cntS.p = (int32_t*)(small + ls.cntS);
+  s.bits.p = (uint32_t*)(small + ls.bits);
+  s.touched.p = (uint32_t*)(small + ls.touched);
+  s.lbase.p = (int32_t*)(small + ls.lbase);
   s.misc = (MEMisc*)(small + ls.misc);
   s.tab = tab_int;
+  return s;
+}
+
+// Decode one frame of code `gd` with thread group `x` on state `s`.
+template <int A, int SCHED, class G, class X>
+__device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const GraphDesc& gd, const G& g,
+                                         const FrameIO& io, MEState<A, X>& s) {
+  using M_ = typename Arith<A>::msg;
+  using L_ = typename Arith<A>::llr;
+  using D_ = typename Arith<A>::dval;
+  const int tid = x.tid, nt = x.nt, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int N = gd.N, E = gd.E, M = gd.M;
+  const int np = a.n_p, ng = a.n_g;
   {
     // fixed point of the FP32 L~ sums: d_v,max * llr_clip * 2^k < 2^30
     const int k = min(24, 29 - ilogbf((float)gd.dv_max * a.llr_clip));
@@ -420,7 +505,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
     ms->ncu = 0;
     ms->npp = 0;
   }
-  if (__syncthreads_or(bad)) {
+  if (x.sync_or(bad, &ms->orflag)) {
     for (int n = tid; n < N; n += nt) {
       if (io.hard) io.hard[n] = 0;
       if (io.llr_out) io.llr_out[n] = (float)s.lam[n];
@@ -446,7 +531,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
       atomicAdd(&ms->unsat, 1);
     }
   }
-  __syncthreads();
+  x.sync();
   for (int n0 = warp * 32; n0 < N; n0 += nt) {  // warp-uniform trip count
     const int n = n0 + lane;
     const bool act = n < N;
@@ -466,16 +551,16 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
       s.grp[n] = (uint8_t)gi;
     }
     const unsigned am = __ballot_sync(kFull, act);
-    if (act) agg_add(s.cnt, gi, 1, am);
+    if (act) agg_add(&s.cnt[gi], gi, 1, am);
   }
-  __syncthreads();
+  x.sync();
 
   int64_t count = 0;
   uint32_t step = 0;
   bool stop = a.check_interval > 0 && ms->unsat == 0;
   if (!stop && io.max_updates > 0) {  // Alg. 5 line 4 / Alg. 6 line 4
-    alg4<A>(s, N, np, ng, 0, step, frame, a.seed);
-    compact_selection<A>(N, s, np);
+    alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed);
+    compact_selection<A, X>(x, N, s, np);
   }
   // L~_j, D_j of VN j (j < 0: idle lane) unless already rewritten in this
   // step; group and group sizes follow.  All lanes of the warp call it.
@@ -497,8 +582,8 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
     }
     const unsigned cm = __ballot_sync(kFull, ch);
     if (ch) {
-      agg_add(s.cnt, go, -1, cm);
-      agg_add(s.cnt, gn, 1, cm);
+      agg_add(&s.cnt[go], go, -1, cm);
+      agg_add(&s.cnt[gn], gn, 1, cm);
     }
   };
   while (!stop && count < io.max_updates) {
@@ -566,7 +651,6 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
         flip = (lold < (L_)0) != (lnew < (L_)0);
         s.L[p] = lnew;
         s.est[k] = (int)bi;
-        s.best[k] = 0ull;
         if (io.trace) io.trace[count + k] = (int)bi;
       }
       flip = __shfl_sync(kFull, flip, vteam * Wv);
@@ -585,11 +669,16 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
         first = !(atomicOr(&s.cbits[m >> 5], bit) & bit);
       }
       const unsigned bal = __ballot_sync(kFull, aff);
+      int base = 0;
       if (bal) {
-        int base = 0;
         if (lane == 0) base = atomicAdd(&ms->ncn, __popc(bal));
         base = __shfl_sync(kFull, base, 0);
         if (aff) s.cnl[base + __popc(bal & lanemask_lt())] = make_int2(m, k);
+      }
+      if (act && q == 0) {  // p's pairs are one block of the list: (first << 32) | count
+        const unsigned tm = (Wv == 32 ? kFull : ((1u << Wv) - 1u)) << (vteam * Wv);
+        const unsigned below = (1u << (vteam * Wv)) - 1u;
+        s.best[k] = ((unsigned long long)(unsigned)(base + __popc(bal & below)) << 32) | (unsigned)__popc(bal & tm);
       }
       const unsigned bf = __ballot_sync(kFull, first);
       if (bf) {
@@ -599,7 +688,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
         if (first) s.cul[base + __popc(bf & lanemask_lt())] = m;
       }
     }
-    __syncthreads();
+    x.sync();
     const int ncn = ms->ncn, ncu = ms->ncu;
     // -- precomputed C2V of every affected check (once per check); the L~ sums
     //    of its variables follow by exact deltas
@@ -615,7 +704,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
         if (delta != 0) atomicAdd(&s.Lt[j], delta);
       }
     }
-    __syncthreads();
+    x.sync();
     // -- L~_j, D_j next to the affected checks and of every p
     for (int w = tid; w < Mw; w += nt) s.cbits[w] = 0u;
     for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
@@ -631,7 +720,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
       const int k = k0 + lane;
       refresh_vn(k < nsel ? s.sel[k] : -1);
     }
-    __syncthreads();
+    x.sync();
     count += nsel;
     ++step;
     if (a.check_interval > 0 && (count / a.check_interval) > ((count - nsel) / a.check_interval) &&
@@ -639,12 +728,12 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
       break;
     if (count >= io.max_updates) break;
     if (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
-      alg4<A>(s, N, np, ng, 0, step, frame, a.seed);  // Alg. 5 line 4
-      compact_selection<A>(N, s, np);
+      alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed);  // Alg. 5 line 4
+      compact_selection<A, X>(x, N, s, np);
       continue;
     }
     // -- Alg. 6 lines 6-10, candidates: per (check i, owner p) the best
-    //    j in N(i)\p by (D_j, lower index)
+    //    j in N(i)\p by (D_j, lower index), written over the pair
     for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
       const int t = t0 + team;
       unsigned long long key = 0ull;
@@ -664,9 +753,9 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
         const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
         key = ok > key ? ok : key;
       }
-      if (r == 0 && key != 0ull) atomicMax(&s.best[k], key);
+      if (r == 0 && t < ncn) s.cand[t] = key;
     }
-    __syncthreads();
+    x.sync();
     // -- P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of Sec. 5.A:
     //    N(m*_p)\p), de-duplicated in the selection bitmap
     for (int k0 = warp * 32; k0 < nsel; k0 += nt) {  // warp-uniform trip count
@@ -675,7 +764,13 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
       int j = 0;
       if (k < nsel) {
         const int p = s.sel[k];
-        unsigned long long bk = s.best[k];
+        const unsigned long long rg = s.best[k];
+        const int first = (int)(rg >> 32), npair = (int)(rg & 0xffffffffull);
+        unsigned long long bk = 0ull;
+        for (int i = first; i < first + npair; ++i) {
+          const unsigned long long v = s.cand[i];
+          bk = v > bk ? v : bk;
+        }
         if (g.vn(p).d == 1) {
           const typename G::C cc = g.cn(g.ecn(s.est[k]));
           bk = 0ull;
@@ -699,14 +794,15 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
         base = __shfl_sync(kFull, base, 0);
         if (add) {
           s.excl[base + __popc(am & lanemask_lt())] = j;
-          agg_add(s.cntS, s.grp[j], 1, am);  // per-group count of P' for Algorithm 4's top-up
+          const int gj = s.grp[j];
+          agg_add(&s.cntS[gj], gj, 1, am);  // per-group count of P' for Algorithm 4's top-up
         }
       }
     }
-    __syncthreads();
+    x.sync();
     const int npp = ms->npp;
-    if (npp < np) alg4<A>(s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
-    compact_selection<A>(N, s, np);
+    if (npp < np) alg4<A, X>(x, s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
+    compact_selection<A, X>(x, N, s, np);
   }
 
   for (int n = tid; n < N; n += nt) {
@@ -717,7 +813,7 @@ __device__ __forceinline__ void me_frame(const DecodeArgs& a, const GraphDesc& g
     if (io.updates) *io.updates = count;
     if (io.converged) *io.converged = ms->unsat == 0 ? 1 : 0;
   }
-  __syncthreads();
+  x.sync();
 }
 
 // Registers: FP32 frames are limited to two CTAs per SM by shared memory, so two
@@ -737,8 +833,9 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_k
   if (A == kINT6)
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   unsigned char* big = smem_raw + a.graph_smem;
-  me_frame<A, SCHED, G>(a, a.g, g, batch_io(a, blockIdx.x, A == kINT6 ? 1 : 4), big, big + a.smem_per_frame,
-                        tab_int);
+  const CtaX x;
+  MEState<A, CtaX> s = cta_state<A>(a.g, a, big, big + a.smem_per_frame, tab_int);
+  me_frame<A, SCHED, G, CtaX>(x, a, a.g, g, batch_io(a, blockIdx.x, A == kINT6 ? 1 : 4), s);
 }
 
 // Global-memory form: CTA c owns state slot c of a.gstate and decodes frames
@@ -751,8 +848,10 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_k
   if (A == kINT6)
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   unsigned char* big = (unsigned char*)a.gstate + (int64_t)blockIdx.x * a.gstate_stride;
+  const CtaX x;
+  MEState<A, CtaX> s = cta_state<A>(a.g, a, big, smem_raw + a.graph_smem, tab_int);
   for (int64_t b = blockIdx.x; b < a.batch; b += gridDim.x)
-    me_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), big, smem_raw + a.graph_smem, tab_int);
+    me_frame<A, SCHED, G, CtaX>(x, a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), s);
 }
 
 // Queue form: CTAs take work items (frames of any of up to 16 lifted codes, each
@@ -805,8 +904,101 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_queue_ke
     io.max_updates = it.max_updates;
     io.frame = it.frame_index;
     const int big = me_big(A, s_gd.M, s_gd.N, s_gd.E).total;
-    me_frame<A, SCHED, QCGraph>(q.a, s_gd, g, io, big <= q.smem_state_bytes ? sstate : gslot, small, tab_int);
+    const CtaX x;
+    MEState<A, CtaX> s = cta_state<A>(s_gd, q.a, big <= q.smem_state_bytes ? sstate : gslot, small, tab_int);
+    me_frame<A, SCHED, QCGraph, CtaX>(x, q.a, s_gd, g, io, s);
   }
+}
+
+// State views of a frame spread over the CTAs of a cluster (plan a.cl); the
+// state area starts at `base` in every CTA's shared memory.
+template <int A>
+__device__ __forceinline__ MEState<A, ClusterX> cluster_state(const DecodeArgs& a, unsigned char* base,
+                                                              const int16_t* tab_int) {
+  using M_ = typename Arith<A>::msg;
+  using L_ = typename Arith<A>::llr;
+  using D_ = typename Arith<A>::dval;
+  const ClusterPlan& c = a.cl;
+  MEState<A, ClusterX> s;
+#define LDPC_DARR(field, T, k) s.field = DArr<T>{(T*)(base + c.off[k]), (int)c.shift[k], (int)c.rank0[k]}
+  LDPC_DARR(C, M_, 0);
+  LDPC_DARR(P, M_, 1);
+  LDPC_DARR(lam, L_, 2);
+  LDPC_DARR(L, L_, 3);
+  LDPC_DARR(D, D_, 4);
+  LDPC_DARR(Lt, int32_t, 5);
+  LDPC_DARR(grp, uint8_t, 6);
+  LDPC_DARR(par, uint32_t, 7);
+  LDPC_DARR(sel, int32_t, 8);
+  LDPC_DARR(est, int32_t, 9);
+  LDPC_DARR(best, unsigned long long, 10);
+  LDPC_DARR(excl, int32_t, 11);
+  LDPC_DARR(cnl, int2, 12);
+  LDPC_DARR(cand, unsigned long long, 12);
+  LDPC_DARR(cul, int32_t, 13);
+  LDPC_DARR(cbits, uint32_t, 14);
+  LDPC_DARR(cnt, int32_t, 15);
+  LDPC_DARR(cntS, int32_t, 16);
+  LDPC_DARR(bits, uint32_t, 17);
+  LDPC_DARR(touched, uint32_t, 18);
+  LDPC_DARR(lbase, int32_t, 19);
+#undef LDPC_DARR
+  s.misc = cg::this_cluster().map_shared_rank((MEMisc*)(base + c.off[20]), (unsigned)c.rank0[20]);
+  s.tab = tab_int;
+  return s;
+}
+
+// Cluster form: the CTAs of cluster c decode frames c, c + clusters, ... with
+// the frame state spread over their shared memory (one CTA per SM).
+template <int A, int SCHED, class G, int TPB>
+__global__ void __launch_bounds__(TPB, 1) me_cluster_kernel(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int16_t tab_int[256];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  if (A == kINT6)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
+  const cg::cluster_group cl = cg::this_cluster();
+  unsigned char* base = smem_raw + a.graph_smem;
+  MEState<A, ClusterX> s = cluster_state<A>(a, base, tab_int);
+  if (cl.block_rank() == (unsigned)a.cl.rank0[20] && threadIdx.x == 0)
+    ((MEMisc*)(base + a.cl.off[20]))->orflag = 0;
+  const ClusterX x;
+  x.sync();  // every CTA of the cluster runs before any distributed access
+  const int64_t ncl = gridDim.x / a.cl.cs;
+  for (int64_t b = blockIdx.x / a.cl.cs; b < a.batch; b += ncl)
+    me_frame<A, SCHED, G, ClusterX>(x, a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), s);
+  x.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <int A, int S, class G, int TPB>
+cudaError_t launch_me_cluster_t(const DecodeArgs& a, cudaStream_t st) {
+  auto k = me_cluster_kernel<A, S, G, TPB>;
+  const size_t smem = (size_t)a.graph_smem + (size_t)a.cl.bytes;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (a.cl.cs > 8) {
+    err = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.cl.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(TPB, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)a.cl.cs, 1, 1);
+  int clusters = 0;
+  err = cudaOccupancyMaxActiveClusters(&clusters, (void*)k, &cfg);
+  if (err != cudaSuccess) return err;
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  const int64_t n = std::min<int64_t>(a.batch, clusters);
+  cfg.gridDim = dim3((unsigned)(n * a.cl.cs), 1, 1);
+  return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 template <int A, int S, int TPB>
@@ -880,6 +1072,69 @@ cudaError_t me_queue_blocks_per_sm(int arith, int sched, int threads, size_t sme
   }
   if (lmd) return big ? me_queue_occ<kINT6, kMELMD, 512>(smem, out) : me_queue_occ<kINT6, kMELMD, 256>(smem, out);
   return big ? me_queue_occ<kINT6, kMECIRBP, 512>(smem, out) : me_queue_occ<kINT6, kMECIRBP, 256>(smem, out);
+}
+
+bool me_cluster_plan(int arith, const GraphDesc& g, int n_p, int n_g, int cs, int64_t avail, ClusterPlan* out) {
+  const int msg = arith == kINT6 ? 1 : 4, llr = arith == kINT6 ? 2 : 4, dv = arith == kINT6 ? 2 : 4;
+  const int64_t ncnl = (int64_t)n_p * (g.dv_max > 1 ? g.dv_max - 1 : 1);
+  const int64_t Mw = (g.M + 31) / 32, Nw = (g.N + 31) / 32;
+  // elements and element sizes in array order
+  const int64_t n[kClusterArrays] = {g.E, g.E, g.N, g.N, g.N, g.N, g.N, Mw,
+                                     n_p, n_p, n_p, n_p, std::max<int64_t>(ncnl, kCap), ncnl, Mw, n_g, n_g,
+                                     Nw, Nw, 33, 1};
+  const int sz[kClusterArrays] = {msg, msg, llr, llr, dv, 4, 1, 4, 4, 4, 8, 4, 8, 4, 4, 4, 4, 4, 4, 4,
+                                  (int)sizeof(MEMisc)};
+  ClusterPlan p;
+  std::memset(&p, 0, sizeof(p));
+  p.cs = cs;
+  std::vector<int64_t> used((size_t)cs, 0);
+  auto a16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
+  auto spread = [&](int k) {  // same offset in every rank, 2^shift >= ceil(n / cs) elements each
+    int sh = 2;
+    while (((int64_t)1 << sh) * cs < n[k]) ++sh;
+    int64_t at = 0;
+    for (int64_t u : used) at = std::max(at, u);
+    p.off[k] = (int32_t)at;
+    p.shift[k] = (int8_t)sh;
+    p.rank0[k] = 0;
+    for (auto& u : used) u = at + a16(((int64_t)1 << sh) * sz[k]);
+  };
+  for (int k = 0; k < 8; ++k) spread(k);
+  for (int k = 8; k < kClusterArrays; ++k) {
+    int sh = 2;
+    while (((int64_t)1 << sh) < n[k]) ++sh;
+    const int64_t bytes = a16(((int64_t)1 << sh) * sz[k]);
+    int best = 0;
+    for (int r = 1; r < cs; ++r)
+      if (used[(size_t)r] < used[(size_t)best]) best = r;
+    if (used[(size_t)best] + bytes <= avail) {  // whole array in the least used rank
+      p.off[k] = (int32_t)used[(size_t)best];
+      p.shift[k] = (int8_t)sh;
+      p.rank0[k] = (int8_t)best;
+      used[(size_t)best] += bytes;
+    } else {
+      spread(k);
+    }
+  }
+  int64_t mx = 0;
+  for (int64_t u : used) mx = std::max(mx, u);
+  if (mx > avail || mx > 0x7fffffff) return false;
+  p.bytes = (int32_t)mx;
+  *out = p;
+  return true;
+}
+
+cudaError_t launch_me_cluster(const DecodeArgs& a, int arith, int sched, int threads, cudaStream_t s) {
+  if (a.batch == 0) return cudaSuccess;
+  const bool lmd = sched == kMELMD, big = threads == 512;
+#define LDPC_CL(AR, SC, GR) (big ? launch_me_cluster_t<AR, SC, GR, 512>(a, s) : launch_me_cluster_t<AR, SC, GR, 256>(a, s))
+  if (arith == kFP32) {
+    if (a.g.is_qc) return lmd ? LDPC_CL(kFP32, kMELMD, QCGraph) : LDPC_CL(kFP32, kMECIRBP, QCGraph);
+    return lmd ? LDPC_CL(kFP32, kMELMD, TabGraph) : LDPC_CL(kFP32, kMECIRBP, TabGraph);
+  }
+  if (a.g.is_qc) return lmd ? LDPC_CL(kINT6, kMELMD, QCGraph) : LDPC_CL(kINT6, kMECIRBP, QCGraph);
+  return lmd ? LDPC_CL(kINT6, kMELMD, TabGraph) : LDPC_CL(kINT6, kMECIRBP, TabGraph);
+#undef LDPC_CL
 }
 
 size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g) {

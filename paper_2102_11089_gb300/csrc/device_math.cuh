@@ -120,10 +120,10 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // Check team: W lanes (power of two) handle check m (m < 0: idle).  Lane r < dc
 // owns edge e = base + r towards variable j; V2C = L_j - C[e] (eq. 1); `out`
 // receives the exclude-one combination over the other edges (eq. 2 / min-sum).
-// All lanes of the warp must call it (width-W shuffles).  Returns dc.
-template <int A, class G>
-__device__ __forceinline__ int team_c2v(const G& g, const typename Arith<A>::msg* C,
-                                        const typename Arith<A>::llr* L, int m, int r, int W,
+// All lanes of the warp must call it (width-W shuffles).  Returns dc.  CA and
+// LA index like arrays (pointers, or the decoders' array views).
+template <int A, class G, class CA, class LA>
+__device__ __forceinline__ int team_c2v(const G& g, const CA& C, const LA& L, int m, int r, int W,
                                         float clip, int& e, int& j, typename Arith<A>::msg& out) {
   int dc = 0;
   e = 0;

@@ -37,6 +37,19 @@ struct GraphDesc {
 };
 
 // Everything a decode kernel needs, passed by value.
+// Cluster form of the multi-edge decoders: where each frame-state array lives
+// in the shared memory of the CTAs of a cluster.  Element i of array k is in
+// rank rank0[k] + (i >> shift[k]), at byte off[k] + (i & (2^shift[k] - 1)) *
+// element size from the start of that CTA's state area.
+constexpr int kClusterArrays = 21;  // C P lam L D Lt grp par | sel est best excl cnl cul cbits cnt cntS bits touched lbase misc
+struct ClusterPlan {
+  int32_t cs;     // CTAs per cluster (0: not the cluster form)
+  int32_t bytes;  // state bytes per CTA
+  int32_t off[kClusterArrays];
+  int8_t shift[kClusterArrays];
+  int8_t rank0[kClusterArrays];
+};
+
 struct DecodeArgs {
   GraphDesc g;
   const void* llr;  // [batch][N] float (FP32) or int8 (INT6)
@@ -63,6 +76,7 @@ struct DecodeArgs {
   int32_t graph_smem;    // bytes of staged graph tables at the start of shared memory
   int32_t team_w;        // lanes per check team: power of two >= max check degree
   int32_t cta_threads;   // multi-edge CTA size (256 or 512)
+  ClusterPlan cl;         // cluster form (cl.cs > 0)
   int16_t ci_table[256];  // INT6: round(32767 tanh(q * q_step / 2)), q = -127..127
 };
 
@@ -179,6 +193,10 @@ cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem
 // resident CTAs per SM of the queue kernels with `smem` bytes of dynamic shared memory
 cudaError_t me_queue_blocks_per_sm(int arith, int sched, int threads, size_t smem, int* out);
 cudaError_t se_queue_blocks_per_sm(int arith, size_t smem, int* out);
+// Cluster form: plan the frame state of code g over `cs` CTAs with `avail`
+// bytes of state each (false if it does not fit), and launch it (a.cl set).
+bool me_cluster_plan(int arith, const GraphDesc& g, int n_p, int n_g, int cs, int64_t avail, ClusterPlan* out);
+cudaError_t launch_me_cluster(const DecodeArgs& a, int arith, int sched, int threads, cudaStream_t s);
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
 cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s);
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s);

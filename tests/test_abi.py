@@ -129,7 +129,7 @@ def test_decode_validation_needs_no_gpu(lib):
     # batch 0 is a no-op
     assert lib.ldpc_decode(code._h, null, 0, ctypes.byref(p), null, null, null, null, null, null) == 0
     bad = [("schedule", 9), ("arith", 5), ("max_updates", -1), ("gamma", 1.5), ("llr_clip", 0.0), ("llr_clip", 2e4),
-           ("tune", 0x40), ("tune", 3), ("check_interval", -2)]
+           ("tune", 0x100), ("tune", 3), ("check_interval", -2)]
     for field, val in bad:
         q = L.make_params("lmd-cirbp", max_updates=10)
         setattr(q, field, val)
@@ -139,6 +139,12 @@ def test_decode_validation_needs_no_gpu(lib):
         q = L.make_params("me-cirbp", max_updates=10, n_p=n_p)
         assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
                                null) == -1
+    q = L.make_params("lmd-cirbp", max_updates=10, form=L.FORM_CLUSTER)  # single-edge: no cluster form
+    assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
+                           null) == -5
+    q = L.make_params("me-cirbp", max_updates=10, form=4)
+    assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
+                           null) == -1
     q = L.make_params("rbp", "int6", max_updates=10, q_step=0.0)
     assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
                            null) == -1
@@ -178,6 +184,6 @@ def test_queue_validation_needs_no_gpu(lib):
         assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -5
     r = L.make_params("me-cirbp", n_p=0)
     assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
-    r = L.make_params("me-cirbp", tune=0x80)
+    r = L.make_params("me-cirbp", tune=0x100)
     assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
     assert L.WORK_ITEM_DTYPE.itemsize == 40

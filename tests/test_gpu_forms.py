@@ -86,3 +86,60 @@ def test_shared_form_refuses_too_large_code():
     with pytest.raises(L.LdpcError) as e:
         L.decode(code, x, schedule="lmd-cirbp", max_updates=10, form=L.FORM_SMEM)
     assert e.value.name == "LDPC_ERR_UNSUPPORTED"
+
+
+def _all_outputs(code, x, torch, **kw):
+    p = L.make_params(**kw)
+    out = L.decode(code, x, p, want_trace=True, want_llr=True)
+    L.sync()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("arith", ["int6", "fp32"])
+@pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "me-cirbp"])
+def test_cluster_form_equals_global_form_bg2_z128(schedule, arith):
+    # n = 6656: frame state spread over the shared memory of a cluster
+    spec = qc("bg2", 128)
+    code = make_code(spec)
+    lam = llrs(spec, 40, 1.0, 31)
+    x = torch.from_numpy(wl.quantize_llrs(lam, 0.5) if arith == "int6" else lam).cuda()
+    kw = dict(schedule=schedule, arith=arith, max_updates=2 * code.E, gamma=0.1, n_p=64, n_g=16, seed=5)
+    ref = _all_outputs(code, x, torch, form=L.FORM_GLOBAL, **kw)
+    for tune in [0, 1 << 6, 2 << 6]:
+        got = _all_outputs(code, x, torch, form=L.FORM_CLUSTER, tune=tune, **kw)
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), (tune, k)
+    got = _all_outputs(code, x, torch, form=L.FORM_AUTO, **kw)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+
+
+def test_cluster_form_small_code_and_sixteen_ctas():
+    # a code that fits one CTA, forced onto a cluster of 2 (smallest) and of 16
+    # (non-portable size: either it runs and agrees, or it is refused)
+    spec = qc("wifi", 96)
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 300, 1.5, 9), 0.5)
+    x = torch.from_numpy(q).cuda()
+    kw = dict(schedule="me-lmd-cirbp", arith="int6", max_updates=3 * code.E, gamma=0.1, n_p=32, n_g=16, seed=2)
+    ref = _all_outputs(code, x, torch, form=L.FORM_SMEM, **kw)
+    got = _all_outputs(code, x, torch, form=L.FORM_CLUSTER, **kw)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+    try:
+        got = _all_outputs(code, x, torch, form=L.FORM_CLUSTER, tune=3 << 6, **kw)
+    except L.LdpcError as e:
+        assert e.name == "LDPC_ERR_UNSUPPORTED"
+    else:
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+
+
+def test_cluster_form_bg1_z384_matches_oracle_int6():
+    spec = qc("bg1", 384)
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 2, 1.2, 41), 0.5)
+    kw = dict(schedule="me-lmd-cirbp", max_updates=code.E // 2, gamma=0.1, n_p=256, n_g=16, seed=8)
+    g = run_gpu(code, q, torch, arith="int6", form=L.FORM_CLUSTER, **kw)
+    o = run_oracle(spec, q, "int6", **kw)
+    assert_bitexact(g, o, "me-lmd-cirbp")
