@@ -84,9 +84,11 @@ struct ClusterX {
     nt = (int)(c.num_blocks() * blockDim.x);
   }
   // release/acquire cluster barrier; the "memory" clobber also keeps the
-  // compiler from moving shared-memory accesses across it
+  // compiler from moving shared-memory accesses across it.  Not the .aligned
+  // form: the compiler does not know this asm needs a converged warp, and an
+  // .aligned barrier reached by a diverged warp is undefined.
   __device__ __forceinline__ void sync() const {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
   }
   // `flag` (one int of the cluster, zero on entry) is reset by thread 0 after use
   __device__ __forceinline__ int sync_or(int v, int* flag) const {
@@ -392,14 +394,16 @@ __device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int
       if (lane >= o) incl += y;
     }
     s.lbase[lane] = incl - c;
-    if (lane == 31) {
-      s.misc->nsel = min(incl, np);
-      s.misc->ncn = 0;
-      s.misc->ncu = 0;
-      s.misc->npp = 0;
-    }
+    if (lane == 31) s.misc->nsel = min(incl, np);
   }
   x.sync();
+  // the step counters are reset only here: until the barrier above some
+  // thread may still be reading npp (whether to run Algorithm 4)
+  if (x.tid == 0) {
+    s.misc->ncn = 0;
+    s.misc->ncu = 0;
+    s.misc->npp = 0;
+  }
   for (int l = warp; l < 32; l += nw) {
     int pos = s.lbase[l];
     if (pos >= np) continue;
@@ -959,11 +963,11 @@ __global__ void __launch_bounds__(TPB, 1) me_cluster_kernel(const DecodeArgs a) 
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   const cg::cluster_group cl = cg::this_cluster();
   unsigned char* base = smem_raw + a.graph_smem;
-  MEState<A, ClusterX> s = cluster_state<A>(a, base, tab_int);
   if (cl.block_rank() == (unsigned)a.cl.rank0[20] && threadIdx.x == 0)
     ((MEMisc*)(base + a.cl.off[20]))->orflag = 0;
   const ClusterX x;
-  x.sync();  // every CTA of the cluster runs before any distributed access
+  x.sync();  // every CTA of the cluster runs before any distributed address is formed
+  MEState<A, ClusterX> s = cluster_state<A>(a, base, tab_int);
   const int64_t ncl = gridDim.x / a.cl.cs;
   for (int64_t b = blockIdx.x / a.cl.cs; b < a.batch; b += ncl)
     me_frame<A, SCHED, G, ClusterX>(x, a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), s);
