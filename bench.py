@@ -80,9 +80,14 @@ def config_dict(args, code):
 
 
 class Clocks:
+    """nvidia-smi clock / throttle samples every 200 ms.  start() returns once the
+    first sample arrived: on a freshly booted box nvidia-smi's start-up takes
+    seconds and stalled the GPU work submitted meanwhile."""
+
     def __init__(self):
         self.samples = []
         self.proc = None
+        self.ready = threading.Event()
 
     def start(self):
         try:
@@ -93,12 +98,19 @@ class Clocks:
                  "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
+            self.ready.wait(timeout=60)
         except FileNotFoundError:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
             self.samples.append([x.strip() for x in line.split(",")])
+            self.ready.set()
+        self.ready.set()
+
+    def mark(self):
+        """Keep only the samples taken from now on (the timed region)."""
+        self.samples = []
 
     def stop(self, gpu_index=0):
         if self.proc is None:
@@ -317,13 +329,19 @@ def run_ours(args):
     frame_base = rank * (10 ** 9)
     dec_ev = []
 
+    ch_ev = []
+
     def step(i, record=False):
         off = frame_base + i * B
+        if record:
+            c0 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
         L.awgn_llr(code, eb, seed=2021, frame_offset=off, out=llr, qout=qllr,
                    quantize=qllr is not None, stream=stream)
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            ch_ev.append((c0, e0))
         L.decode(code, qllr if qllr is not None else llr, params, out=out, stream=stream)
         if record:
             e1.record(stream)
@@ -340,17 +358,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    upd_hist = torch.empty((args.steps, B), dtype=torch.int64, device=device)
+    upd_hist[0].copy_(out["updates"])  # first use of the copy path outside the timed region
+    torch.cuda.synchronize()
+    clocks.mark()
     t0.record(stream)
-    upd_list = []
     for i in range(args.steps):
         step(args.warmup + i, record=True)
-        upd_list.append(out["updates"].sum())  # device-side reduction, read after timing
+        upd_hist[i].copy_(out["updates"])  # device-to-device copy; summed after timing
     t1.record(stream)
     torch.cuda.synchronize()
     barrier(world, device)
     ms = t0.elapsed_time(t1)
     clk = clocks.stop(local)
-    upd_total = int(sum(int(u.item()) for u in upd_list))
+    upd_total = int(upd_hist.sum().item())
     fer = fer_of(out)
     conv = float((out["converged"] & 1).float().mean().item())
     mean_upd = float(out["updates"].float().mean().item())
@@ -358,6 +379,10 @@ def run_ours(args):
     value = world * B * args.steps * K / (ms_max * 1e-3) / 1e9
     dec_ms = [a.elapsed_time(b) for a, b in dec_ev]
     dec_avg = float(np.mean(dec_ms))
+    ch_avg = float(np.mean([a.elapsed_time(b) for a, b in ch_ev]))
+    # time of the timed region not inside a channel or decode launch (host enqueue
+    # stalls, bookkeeping reductions); near zero when the stream stays busy
+    gap_ms = ms / args.steps - dec_avg - ch_avg
 
     # ---- roofline of the decode kernel: algorithmic shared-memory bytes / time
     peaks, peaks_kind = measured_peaks()
@@ -420,6 +445,7 @@ def run_ours(args):
                 "data": "synthetic (seeded Philox AWGN, all-zero codeword, seeded stand-in code)",
                 "config": config_dict(args, code), "fer": fer, "frames_converged": conv,
                 "mean_updates_per_frame": mean_upd, "decode_ms_per_launch": dec_avg,
+                "channel_ms_per_launch": ch_avg, "other_ms_per_step": gap_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, **extras}
         print(json.dumps(line))

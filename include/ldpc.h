@@ -201,10 +201,12 @@ ldpc_status_t ldpc_awgn_llr(const ldpc_code_t *code, const float *ebn0_db, int64
  *             (INT6: the integer value)
  * Stops at a zero syndrome (checked per check_interval) or at the budget.
  * Execution form (params->form = LDPC_FORM_AUTO): frame state in shared
- * memory when it fits one CTA; else, for the multi-edge schedules, spread
- * over the shared memory of a thread-block cluster (the smallest of 2, 4, 8
- * or 16 CTAs that holds it and can be resident); else global memory.  The
- * form never changes a result.
+ * memory when it fits one CTA; else, for the multi-edge schedules and a batch
+ * of at most twice the resident clusters (SMs / cluster size), spread over the
+ * shared memory of a thread-block cluster (the smallest of 2, 4, 8 or 16 CTAs
+ * that holds it and can be resident); else global memory.  A cluster size in
+ * tune bits 6-7 selects the cluster form whenever it can run.  The form never
+ * changes a result.
  * Errors: INVALID_ARG, UNSUPPORTED (no execution form fits; LDPC_FORM_CLUSTER
  * with a single-edge or flooding schedule), CUDA, NOMEM. */
 ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batch,

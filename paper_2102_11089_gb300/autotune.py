@@ -2,9 +2,10 @@
 
 The decode kernels take launch-shape hints in ``ldpc_decode_params_t.tune``:
 CTA size of the multi-edge kernels (bits 0-1), frames per CTA of the
-single-edge kernels (bits 2-3) and, for the work-queue form, where frame state
+single-edge kernels (bits 2-3), for the work-queue form where frame state
 lives (bits 4-5: shared memory for codes that fit two, three or one CTA per
-SM, or global memory only).  None of them changes a result; they only move
+SM, or global memory only) and the multi-edge cluster form with 4, 8 or 16
+CTAs per cluster (bits 6-7).  None of them changes a result; they only move
 work between threads, CTAs and memories.
 
 The tuner runs a grid search over the hints that apply to a call on a
@@ -37,8 +38,8 @@ def candidates(entry: str, schedule: int) -> list[int]:
         return [pl << 4 for pl in (PLACE_HALF, PLACE_THIRD, PLACE_FULL, PLACE_GLOBAL)]
     if entry != "decode":
         raise ValueError(f"unknown entry point {entry!r}")
-    if multi:
-        return [CTA_256, CTA_512]
+    if multi:  # CTA size; cluster form with 4, 8 or 16 CTAs (bits 6-7)
+        return [CTA_256, CTA_512] + [CTA_512 | (cl << 6) for cl in (1, 2, 3)]
     if schedule == FLOODING:
         return [0]
     return [fpc << 2 for fpc in (0, 1, 2, 3)]
@@ -48,7 +49,8 @@ def describe(tune: int) -> dict:
     cta = {0: "default", 1: 256, 2: 512}[tune & 3]
     fpc = {0: "auto", 1: 2, 2: 4, 3: 8}[(tune >> 2) & 3]
     place = {0: "smem<=1/2 SM", 1: "smem<=1/3 SM", 2: "smem<=1 SM", 3: "global"}[(tune >> 4) & 3]
-    return {"cta_threads": cta, "frames_per_cta": fpc, "queue_state": place}
+    cluster = {0: "auto", 1: 4, 2: 8, 3: 16}[(tune >> 6) & 3]
+    return {"cta_threads": cta, "frames_per_cta": fpc, "queue_state": place, "cluster_ctas": cluster}
 
 
 def cache_key(entry: str, device: str, codes, params) -> str:

@@ -565,15 +565,24 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   }
   const bool fits = (int64_t)per + (int64_t)cta_fixed + gsm <= optin;
   if (p->form == LDPC_FORM_SMEM && !fits) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
-  // Cluster form (multi-edge, on request or for frames too large for one CTA):
-  // the smallest cluster (or the requested size) whose shared memory holds the
-  // frame state and that can be resident; else the global-memory form.
-  if (p->schedule >= LDPC_ME_CIRBP && (p->form == LDPC_FORM_CLUSTER || (p->form == LDPC_FORM_AUTO && !fits))) {
-    const int req = (p->tune >> 6) & 3;
+  // Cluster form (multi-edge): on request (LDPC_FORM_CLUSTER, or a cluster
+  // size in tune bits 6-7), or for frames too large for one CTA when the batch
+  // is small: a cluster decodes a frame about three times sooner than a CTA
+  // with global-memory state but holds cs SMs, so with auto sizing it is taken
+  // while the batch is at most twice the resident clusters.  The smallest
+  // cluster (or the requested size) whose shared memory holds the state and
+  // that can be resident; else the global-memory form.
+  const int req = (p->tune >> 6) & 3;
+  if (p->schedule >= LDPC_ME_CIRBP &&
+      (p->form == LDPC_FORM_CLUSTER || (p->form == LDPC_FORM_AUTO && (req != 0 || !fits)))) {
     const int threads = (p->tune & 3) == 1 ? 256 : 512;
     const int64_t avail = (int64_t)optin - gsm - 1024;
     for (int cs = req ? (2 << req) : 2; cs <= (req ? (2 << req) : 16); cs *= 2) {
       if (!ldpc::me_cluster_plan(arith, *g, p->n_p, p->n_g, cs, avail, &a.cl)) continue;
+      if (p->form == LDPC_FORM_AUTO && req == 0 && batch > 2 * (int64_t)(sms / cs)) {
+        a.cl.cs = 0;  // large batch: the global-memory form keeps every SM busy
+        break;
+      }
       a.cta_threads = threads;
       e = ldpc::launch_me_cluster(a, arith, p->schedule, threads, s);
       if (e == cudaSuccess) return LDPC_OK;
