@@ -568,13 +568,17 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
   }
   // L~_j, D_j of VN j (j < 0: idle lane) unless already rewritten in this
   // step; group and group sizes follow.  All lanes of the warp call it.
-  auto refresh_vn = [&](int j) {
+  // With `want` the new D_j is also returned when another lane rewrites it (its
+  // inputs are final in this phase, so every lane computes the same value).
+  auto refresh_vn = [&](int j, bool want) -> D_ {
     bool ch = false;
     int go = 0, gn = 0;
+    D_ d = (D_)0;
     if (j >= 0) {
       const uint32_t bit = 1u << (j & 31);
-      if (!(atomicOr(&s.touched[j >> 5], bit) & bit)) {
-        const D_ d = ci_me(s, s.L[j], lt_total(s, j));
+      const bool first = !(atomicOr(&s.touched[j >> 5], bit) & bit);
+      if (first || want) d = ci_me(s, s.L[j], lt_total(s, j));
+      if (first) {
         s.D[j] = d;
         gn = group_of(d, ng);
         go = s.grp[j];
@@ -589,6 +593,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
       agg_add(&s.cnt[go], go, -1, cm);
       agg_add(&s.cnt[gn], gn, 1, cm);
     }
+    return d;
   };
   while (!stop && count < io.max_updates) {
     int nsel = ms->nsel;
@@ -709,20 +714,46 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
       }
     }
     x.sync();
-    // -- L~_j, D_j next to the affected checks and of every p
+    // -- L~_j, D_j next to the affected checks and of every p.  ME-LMD-CIRBP runs
+    //    this over the (check i, owner p) pairs and also forms Alg. 6 lines 6-10's
+    //    candidate of each pair: the best j in N(i)\p by (D_j, lower index),
+    //    written over the pair
     for (int w = tid; w < Mw; w += nt) s.cbits[w] = 0u;
-    for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
-      const int t = t0 + team;
-      int j = -1;
-      if (t < ncu) {
-        const typename G::C cc = g.cn(s.cul[t]);
-        if (r < cc.d) j = g.cvn(cc, r);
+    if (SCHED == kMELMD) {
+      for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
+        const int t = t0 + team;
+        int j = -1, k = 0;
+        if (t < ncn) {
+          const int2 ck = s.cnl[t];
+          k = ck.y;
+          const typename G::C cc = g.cn(ck.x);
+          if (r < cc.d) j = g.cvn(cc, r);
+        }
+        const D_ d = refresh_vn(j, true);
+        unsigned long long key = 0ull;
+        if (j >= 0 && j != s.sel[k]) key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          if (o >= W) continue;
+          const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
+          key = ok > key ? ok : key;
+        }
+        if (r == 0 && t < ncn) s.cand[t] = key;
       }
-      refresh_vn(j);
+    } else {
+      for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
+        const int t = t0 + team;
+        int j = -1;
+        if (t < ncu) {
+          const typename G::C cc = g.cn(s.cul[t]);
+          if (r < cc.d) j = g.cvn(cc, r);
+        }
+        refresh_vn(j, false);
+      }
     }
     for (int k0 = warp * 32; k0 < nsel; k0 += nt) {
       const int k = k0 + lane;
-      refresh_vn(k < nsel ? s.sel[k] : -1);
+      refresh_vn(k < nsel ? s.sel[k] : -1, false);
     }
     x.sync();
     count += nsel;
@@ -736,30 +767,6 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
       compact_selection<A, X>(x, N, s, np);
       continue;
     }
-    // -- Alg. 6 lines 6-10, candidates: per (check i, owner p) the best
-    //    j in N(i)\p by (D_j, lower index), written over the pair
-    for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
-      const int t = t0 + team;
-      unsigned long long key = 0ull;
-      int k = 0;
-      if (t < ncn) {
-        const int2 ck = s.cnl[t];
-        k = ck.y;
-        const typename G::C cc = g.cn(ck.x);
-        if (r < cc.d) {
-          const int j = g.cvn(cc, r);
-          if (j != s.sel[k]) key = ((unsigned long long)mkey(s.D[j]) << 32) | (0xffffffffu - (uint32_t)j);
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        if (o >= W) continue;
-        const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
-        key = ok > key ? ok : key;
-      }
-      if (r == 0 && t < ncn) s.cand[t] = key;
-    }
-    x.sync();
     // -- P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of Sec. 5.A:
     //    N(m*_p)\p), de-duplicated in the selection bitmap
     for (int k0 = warp * 32; k0 < nsel; k0 += nt) {  // warp-uniform trip count
