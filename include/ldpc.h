@@ -55,6 +55,8 @@ typedef int32_t ldpc_status_t;
 #define LDPC_LMD_CIRBP 3    /* Algorithm 3 (latest-message-driven CIRBP)            */
 #define LDPC_ME_CIRBP 4     /* Algorithm 5 (N_P edges per step, Algorithm 4)        */
 #define LDPC_ME_LMD_CIRBP 5 /* Algorithm 6                                          */
+#define LDPC_LMDRBP 6       /* Algorithm 2 (latest-message-driven RBP)              */
+#define LDPC_SLMDRBP 7      /* Algorithm 2 without line 10 (simplified LMDRBP)      */
 
 /* arithmetic (ldpc_decode_params_t.arith) */
 #define LDPC_FP32_SUMPRODUCT 0 /* eq. (2) in FP32; input LLRs are float          */
@@ -88,7 +90,7 @@ typedef struct {
 } ldpc_code_info_t;
 
 typedef struct {
-    int32_t schedule;       /* LDPC_FLOODING .. LDPC_ME_LMD_CIRBP                 */
+    int32_t schedule;       /* LDPC_FLOODING .. LDPC_SLMDRBP                      */
     int32_t arith;          /* LDPC_FP32_SUMPRODUCT or LDPC_INT6_MINSUM           */
     double gamma;           /* CIRBP threshold on D (Alg. 1 line 5), in [0, 1)    */
     int32_t n_p;            /* multi-edge: VNs updated per step (N_P, Sec. 6),

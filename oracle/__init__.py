@@ -21,9 +21,9 @@ _LIBPATH = os.path.join(_LIBDIR, "libldpc_oracle.so")
 _lock = threading.Lock()
 _handle = None
 
-FLOODING, RBP, CIRBP, LMD_CIRBP, ME_CIRBP, ME_LMD_CIRBP = range(6)
+FLOODING, RBP, CIRBP, LMD_CIRBP, ME_CIRBP, ME_LMD_CIRBP, LMDRBP, SLMDRBP = range(8)
 SCHEDULES = {"flooding": FLOODING, "rbp": RBP, "cirbp": CIRBP, "lmd-cirbp": LMD_CIRBP,
-             "me-cirbp": ME_CIRBP, "me-lmd-cirbp": ME_LMD_CIRBP}
+             "me-cirbp": ME_CIRBP, "me-lmd-cirbp": ME_LMD_CIRBP, "lmdrbp": LMDRBP, "slmdrbp": SLMDRBP}
 FP, INT = 0, 1
 
 COUNTERS = ["prop", "v2c", "c2v_pre", "ci", "ci_extra", "cmp", "icmp", "steps", "selfcheck",

@@ -32,6 +32,8 @@
  *      counter = (n / 4, step, frame)); equal keys go to the lower index.
  *  R7  Degree-1 rule (Sec. 5.A): if d_v(n*) = 1 the LMD candidate set is
  *      N(m*)\n*; if the candidate set is still empty, the global argmax of D.
+ *      For LMDRBP the candidates are the edges of m* to N(m*)\n*, and an
+ *      empty set falls back to the global residual argmax (its line 3).
  *  R8  Syndrome checked at update count 0 and whenever the count crosses a
  *      multiple of `check_interval` (0 = never); budget in edge updates.
  *  R9  Messages are clipped to +-llr_clip in FP mode (V2C before the tanh rule,
@@ -52,6 +54,8 @@
 #define ORC_LMD_CIRBP 3
 #define ORC_ME_CIRBP 4
 #define ORC_ME_LMD_CIRBP 5
+#define ORC_LMDRBP 6
+#define ORC_SLMDRBP 7
 
 #define ORC_ARITH_FP 0
 #define ORC_ARITH_INT 1
@@ -672,6 +676,50 @@ static void run_lmd_cirbp(fr_t *f) {
     }
 }
 
+/* Candidate edges of Alg. 2 line 9: the residuals of i -> j for            */
+/* i in M(n*)\m*, j in N(i)\n* (just recomputed), or, when d_v(n*) = 1, of  */
+/* m* -> j for j in N(m*)\n* (Sec. 5.A).                                     */
+static amax_t lmdrbp_next(fr_t *f, int nstar, int estar) {
+    const og_t *g = f->g;
+    int mstar = g->e_cn[estar];
+    amax_t a; am_init(&a);
+    int dv = g->vn_ptr[nstar + 1] - g->vn_ptr[nstar];
+    for (int k = g->vn_ptr[nstar]; k < g->vn_ptr[nstar + 1]; k++) {
+        int i = g->e_cn[g->vn_e[k]];
+        if (dv > 1 && i == mstar) continue;
+        for (int e = g->cn_ptr[i]; e < g->cn_ptr[i + 1]; e++)
+            if (g->e_vn[e] != nstar) am_push(&a, e, resid(f, e));
+    }
+    am_count(f, &a);
+    return a;
+}
+
+/* Algorithm 2 (LMDRBP); `simplified` bypasses its line 10 (sLMDRBP).        */
+static void run_lmdrbp(fr_t *f, int simplified) {
+    amax_t a = argmax_R_all(f); /* line 3 */
+    int e = a.idx;
+    double gap = am_gap(&a);
+    while (f->count < f->pr->max_updates) {
+        int64_t before = f->count;
+        int n = f->g->e_vn[e];
+        record(f, e, gap);
+        commit(f, e);                  /* line 4 */
+        refresh_after_commit(f, n, e); /* lines 5-8 */
+        f->count++; f->ctr[CT_STEPS]++;
+        after_step(f);
+        if (check_stop(f, before)) break;
+        a = lmdrbp_next(f, n, e);      /* line 9 */
+        if (a.idx < 0) a = argmax_R_all(f);
+        e = a.idx;
+        gap = am_gap(&a);
+        if (!simplified) {             /* line 10: the best check into n' */
+            amax_t ar = argmax_R_into(f, f->g->e_vn[e]);
+            e = ar.idx;
+            gap = fmin(gap, am_gap(&ar));
+        }
+    }
+}
+
 /* Multi-edge step shared by Algorithms 5 and 6: for every p of the selected */
 /* set, m*_p = argmax R into p on the pre-step state; commit all; then one   */
 /* refresh of every check that received a new V2C and every VN next to one. */
@@ -857,6 +905,8 @@ static void decode_frame(job_t *J, int64_t b) {
         case ORC_LMD_CIRBP: run_lmd_cirbp(&f); break;
         case ORC_ME_CIRBP: run_me_cirbp(&f); break;
         case ORC_ME_LMD_CIRBP: run_me_lmd_cirbp(&f); break;
+        case ORC_LMDRBP: run_lmdrbp(&f, 0); break;
+        case ORC_SLMDRBP: run_lmdrbp(&f, 1); break;
         default: J->rc = ORC_ERR_ARG; break;
         }
     }
@@ -888,8 +938,9 @@ int orc_decode(const int32_t *chk, const int32_t *var, int64_t E, int32_t M, int
                uint8_t *hard, int64_t *updates, uint8_t *converged, int32_t *trace, double *gap,
                double *llr_out, int64_t *counters, double *state_out, int n_threads) {
     if (!pr || (!llr && !qllr) || batch < 0) return ORC_ERR_ARG;
-    if (pr->schedule < 0 || pr->schedule > 5) return ORC_ERR_ARG;
-    if ((pr->schedule >= ORC_ME_CIRBP) && (pr->n_p <= 0 || pr->n_g <= 0)) return ORC_ERR_ARG;
+    if (pr->schedule < 0 || pr->schedule > ORC_SLMDRBP) return ORC_ERR_ARG;
+    if ((pr->schedule == ORC_ME_CIRBP || pr->schedule == ORC_ME_LMD_CIRBP) && (pr->n_p <= 0 || pr->n_g <= 0))
+        return ORC_ERR_ARG;
     if (pr->max_updates < 0) return ORC_ERR_ARG;
     og_t g;
     int rc = og_build(&g, chk, var, E, M, N);

@@ -20,9 +20,9 @@ __all__ = [
     "FP32_SUMPRODUCT", "INT6_MINSUM", "FORM_AUTO", "FORM_SMEM", "FORM_GLOBAL",
 ]
 
-FLOODING, RBP, CIRBP, LMD_CIRBP, ME_CIRBP, ME_LMD_CIRBP = range(6)
+FLOODING, RBP, CIRBP, LMD_CIRBP, ME_CIRBP, ME_LMD_CIRBP, LMDRBP, SLMDRBP = range(8)
 SCHEDULES = {"flooding": FLOODING, "rbp": RBP, "cirbp": CIRBP, "lmd-cirbp": LMD_CIRBP,
-             "me-cirbp": ME_CIRBP, "me-lmd-cirbp": ME_LMD_CIRBP}
+             "me-cirbp": ME_CIRBP, "me-lmd-cirbp": ME_LMD_CIRBP, "lmdrbp": LMDRBP, "slmdrbp": SLMDRBP}
 FP32_SUMPRODUCT, INT6_MINSUM = 0, 1
 FORM_AUTO, FORM_SMEM, FORM_GLOBAL, FORM_CLUSTER = 0, 1, 2, 3
 

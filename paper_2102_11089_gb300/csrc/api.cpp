@@ -483,7 +483,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
                           int32_t* trace, float* llr_out, void* cuda_stream) {
   if (!code || !p) return fail(LDPC_ERR_INVALID_ARG, "code and params are required");
   if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
-  if (p->schedule < LDPC_FLOODING || p->schedule > LDPC_ME_LMD_CIRBP)
+  if (p->schedule < LDPC_FLOODING || p->schedule > LDPC_SLMDRBP)
     return fail(LDPC_ERR_INVALID_ARG, "unknown schedule");
   if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
@@ -492,11 +492,11 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   if (!(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
   if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
-  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 1024))
+  if (ldpc::is_multi_edge(p->schedule) && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 1024))
     return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 1024 required");
   if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0xff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
-  if (p->form == LDPC_FORM_CLUSTER && p->schedule < LDPC_ME_CIRBP)
+  if (p->form == LDPC_FORM_CLUSTER && !ldpc::is_multi_edge(p->schedule))
     return fail(LDPC_ERR_UNSUPPORTED, "the cluster form runs the multi-edge schedules");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
@@ -555,7 +555,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   size_t per = 0, cta_fixed = 0;
   if (p->schedule == LDPC_FLOODING) {
     per = ldpc::flood_smem_per_frame(arith, *g);
-  } else if (p->schedule <= LDPC_LMD_CIRBP) {
+  } else if (ldpc::is_single_edge(p->schedule)) {
     if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
     per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
   } else {
@@ -573,7 +573,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   // cluster (or the requested size) whose shared memory holds the state and
   // that can be resident; else the global-memory form.
   const int req = (p->tune >> 6) & 3;
-  if (p->schedule >= LDPC_ME_CIRBP &&
+  if (ldpc::is_multi_edge(p->schedule) &&
       (p->form == LDPC_FORM_CLUSTER || (p->form == LDPC_FORM_AUTO && (req != 0 || !fits)))) {
     const int threads = (p->tune & 3) == 1 ? 256 : 512;
     const int64_t avail = (int64_t)optin - gsm - 1024;
@@ -602,7 +602,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     const int64_t stride = ((int64_t)per + 255) & ~(int64_t)255;
     int fpc = 1;
     int64_t ctas;
-    if (p->schedule >= LDPC_RBP && p->schedule <= LDPC_LMD_CIRBP) {
+    if (ldpc::is_single_edge(p->schedule)) {
       fpc = (int)std::min<int64_t>(8, batch);
       ctas = std::min<int64_t>((batch + fpc - 1) / fpc, (int64_t)sms * 4);
     } else {
@@ -615,7 +615,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     a.gstate_stride = stride;
     a.gstate_ctas = (int32_t)ctas;
     a.frames_per_cta = fpc;
-  } else if (p->schedule >= LDPC_RBP && p->schedule <= LDPC_LMD_CIRBP) {
+  } else if (ldpc::is_single_edge(p->schedule)) {
     // frames per CTA: fill about half the opt-in shared memory so two CTAs share an SM
     int fpc = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t)std::max(0, optin / 2 - gsm) / per));
     if ((p->tune >> 2) & 3) fpc = 1 << ((p->tune >> 2) & 3);  // 2, 4 or 8 frames by request
@@ -626,7 +626,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     a.frames_per_cta = 1;
   }
   if (p->schedule == LDPC_FLOODING) e = ldpc::launch_flood(a, arith, s);
-  else if (p->schedule <= LDPC_LMD_CIRBP) e = ldpc::launch_se(a, arith, p->schedule, s);
+  else if (ldpc::is_single_edge(p->schedule)) e = ldpc::launch_se(a, arith, p->schedule, s);
   else e = ldpc::launch_me(a, arith, p->schedule, s);
   if (scratch) {
     const cudaError_t e2 = cudaFreeAsync(scratch, s);

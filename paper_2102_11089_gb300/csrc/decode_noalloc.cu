@@ -71,7 +71,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   ldpc::CodeHostView v;
   if (!code || !p || !ldpc::code_host_view(code, &v)) return fail(LDPC_ERR_INVALID_ARG, "code and params are required");
   if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
-  if (p->schedule < LDPC_FLOODING || p->schedule > LDPC_ME_LMD_CIRBP)
+  if (p->schedule < LDPC_FLOODING || p->schedule > LDPC_SLMDRBP)
     return fail(LDPC_ERR_INVALID_ARG, "unknown schedule");
   if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
@@ -80,14 +80,14 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   if (!(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
   if (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f && std::isfinite(p->q_step)))
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
-  if (p->schedule >= LDPC_ME_CIRBP && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255))
+  if (ldpc::is_multi_edge(p->schedule) && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255))
     return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 255 required");
   if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0xff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
   if (v.dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
-  if (p->schedule >= LDPC_RBP && p->schedule <= LDPC_LMD_CIRBP && v.dv_max > 32)
+  if (ldpc::is_single_edge(p->schedule) && v.dv_max > 32)
     return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
 
   int dev = 0;
@@ -174,7 +174,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   if (p->schedule == LDPC_FLOODING) {
     per = ldpc::flood_smem_per_frame(arith, g);
     want = std::min<int64_t>(batch, (int64_t)sms * 2);
-  } else if (p->schedule <= LDPC_LMD_CIRBP) {
+  } else if (ldpc::is_single_edge(p->schedule)) {
     per = ldpc::se_smem_per_frame(arith, p->schedule, g);
     fpc = (int)std::min<int64_t>(8, batch);
     want = std::min<int64_t>((batch + fpc - 1) / fpc, (int64_t)sms * 4);
@@ -196,7 +196,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   a.frames_per_cta = fpc;
   a.smem_per_frame = (int32_t)per;
   if (p->schedule == LDPC_FLOODING) e = ldpc::launch_flood(a, arith, s);
-  else if (p->schedule <= LDPC_LMD_CIRBP) e = ldpc::launch_se(a, arith, p->schedule, s);
+  else if (ldpc::is_single_edge(p->schedule)) e = ldpc::launch_se(a, arith, p->schedule, s);
   else e = ldpc::launch_me(a, arith, p->schedule, s);
   if (e != cudaSuccess) return fail(LDPC_ERR_CUDA, std::string("decode launch: ") + cudaGetErrorString(e));
   return LDPC_OK;

@@ -1,7 +1,8 @@
 // decode_se.cu -- single-edge dynamic schedules, one frame per warp.
 //
-// Residual BP (Sec. 2.A, steps 1-4), CIRBP (Algorithm 1) and LMD-CIRBP
-// (Algorithm 3) commit one check-to-variable (C2V) message per update.  The
+// Residual BP (Sec. 2.A, steps 1-4), CIRBP (Algorithm 1), LMD-CIRBP
+// (Algorithm 3), LMDRBP and sLMDRBP (Algorithm 2, with and without its line 10)
+// commit one check-to-variable (C2V) message per update.  The
 // chain select -> commit -> refresh -> select is serial within a frame, so a
 // frame is one warp; frames are the warps of the CTAs.  Per update:
 //   - lanes k < d_v(n*) own the edges into the target n*: residual argmax
@@ -9,7 +10,8 @@
 //   - the d_v - 1 refreshed checks i in M(n*)\m* (Alg. 1 lines 10-13) are
 //     handled by teams of W lanes, one lane per edge: new V2C inputs, the
 //     exclude-one C2V of eq. (2) (or min-sum) by width-W shuffles, then
-//     L~_j and D_j (eq. 8) of j in N(i)\n*, which are also the LMD candidates.
+//     L~_j and D_j (eq. 8) of j in N(i)\n*, which are also the LMD candidates
+//     (LMD-CIRBP by D_j, LMDRBP by the new residuals of those edges).
 // Per-frame state in shared memory:
 //   C[E] L^C, P[E] L~^C, lam/L[N], D[N], Rmax/Ridx[M] (largest residual per
 //   check, for the global argmax of eq. (5): RBP and CIRBP's fallback), par
@@ -190,8 +192,10 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   __syncwarp();
 
   // ---- schedule loop
+  constexpr bool kLMDR = SCHED == kLMDRBP || SCHED == kSLMDRBP;
   int64_t count = 0;
   int nstar = 0;
+  int enext = -1;  // LMDRBP: edge found by Alg. 2 line 9 for the next update (-1: none)
   bool stop = (a.check_interval > 0 && unsat == 0);
   if (!stop && SCHED == kLMD) {
     uint32_t k;
@@ -203,6 +207,14 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     if (SCHED == kRBP) {
       eglob = global_argmax_R<A>(M, s);
       nstar = g.evn(eglob);
+    } else if (kLMDR) {
+      if (enext < 0) {  // Alg. 2 line 3, and an empty candidate set
+        eglob = global_argmax_R<A>(M, s);
+        nstar = g.evn(eglob);
+      } else {
+        nstar = g.evn(enext);  // n' of line 9; LMDRBP re-selects its check (line 10)
+        if (SCHED == kSLMDRBP) eglob = enext;
+      }
     } else if (SCHED == kCIRBP) {
       uint32_t dkey;
       nstar = global_argmax_D<A>(N, s, dkey);
@@ -270,6 +282,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     //    variables j != n* (also the LMD candidates)
     const int nref = dv - 1;
     uint32_t ck = 0, cidx = 0xffffffffu;
+    uint32_t rck = 0, rcidx = 0xffffffffu;
     if (nref <= tpw) {  // one pass of teams
       const int k = team < kstar ? team : team + 1;
       const int m = __shfl_sync(kFull, my_m, k & 31);
@@ -277,7 +290,10 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
       M_ out;
       const int dc = team_c2v<A, G>(g, s.C, s.L, team < nref ? m : -1, r, W, clip, e, j, out);
       const bool mine = r < dc && j != nstar;
-      if (mine) s.P[e] = out;
+      if (mine) {
+        s.P[e] = out;
+        if (kLMDR) am_update(rck, rcidx, rkey(out, s.C[e]), (uint32_t)e);  // Alg. 2 line 9
+      }
       __syncwarp();
       if (mine) {
         const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
@@ -292,7 +308,10 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
         int e, j;
         M_ out;
         const int dc = team_c2v<A, G>(g, s.C, s.L, i < nref ? m : -1, r, W, clip, e, j, out);
-        if (r < dc && j != nstar) s.P[e] = out;
+        if (r < dc && j != nstar) {
+          s.P[e] = out;
+          if (kLMDR) am_update(rck, rcidx, rkey(out, s.C[e]), (uint32_t)e);  // Alg. 2 line 9
+        }
       }
       __syncwarp();
       for (int i0 = 0; i0 < nref; i0 += tpw) {
@@ -316,6 +335,23 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     ++count;
     if (a.check_interval > 0 && (count % a.check_interval) == 0 && unsat == 0) break;
 
+    // -- LMDRBP: next edge = argmax of the residuals just refreshed (Alg. 2 line
+    //    9), or over the edges of m* to N(m*)\n* when d_v(n*) = 1 (Sec. 5.A);
+    //    none: the global residual argmax next time
+    if (kLMDR) {
+      if (dv == 1) {
+        rck = 0;
+        rcidx = 0xffffffffu;
+        const typename G::C cc = g.cn(mstar);
+        for (int q = lane; q < cc.d; q += 32) {
+          const int e = cc.b + q;
+          if (g.cvn(cc, q) != nstar) am_update(rck, rcidx, rkey(s.P[e], s.C[e]), (uint32_t)e);
+        }
+      }
+      uint32_t key;
+      const uint32_t en = warp_argmax(rck, rcidx, key);
+      enext = en == 0xffffffffu ? -1 : (int)en;
+    }
     // -- LMD: next target = argmax D over U(m*, n*) (Alg. 3 line 11), or over
     //    N(m*)\n* when d_v(n*) = 1 (Sec. 5.A), else the global argmax.
     if (SCHED == kLMD) {
@@ -449,6 +485,8 @@ template <int A, class G>
 cudaError_t launch_sched(const DecodeArgs& a, int sched, cudaStream_t s) {
   if (sched == kRBP) return launch_one<A, kRBP, G>(a, s);
   if (sched == kCIRBP) return launch_one<A, kCIRBP, G>(a, s);
+  if (sched == kLMDRBP) return launch_one<A, kLMDRBP, G>(a, s);
+  if (sched == kSLMDRBP) return launch_one<A, kSLMDRBP, G>(a, s);
   return launch_one<A, kLMD, G>(a, s);
 }
 

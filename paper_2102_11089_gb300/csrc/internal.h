@@ -18,6 +18,11 @@ constexpr int kCIRBP = 2;
 constexpr int kLMD = 3;
 constexpr int kMECIRBP = 4;
 constexpr int kMELMD = 5;
+constexpr int kLMDRBP = 6;   // Algorithm 2
+constexpr int kSLMDRBP = 7;  // Algorithm 2 without line 10
+
+inline __host__ __device__ bool is_multi_edge(int s) { return s == kMECIRBP || s == kMELMD; }
+inline __host__ __device__ bool is_single_edge(int s) { return s >= kRBP && !is_multi_edge(s) && s <= kSLMDRBP; }
 
 // Device view of a code (canonical CSR edge order: by check, then variable).
 // `tab` = cn_ptr[M+1] | e_vn[E] | e_cn[E] | vn_ptr[N+1] | vn_e[E] (int32), always

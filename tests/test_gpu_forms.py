@@ -12,7 +12,7 @@ from gpu_helpers import (assert_bitexact, fer_in_interval, llrs, make_code, qc, 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-ALL = ["flooding", "rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp"]
+ALL = ["flooding", "rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp", "lmdrbp", "slmdrbp"]
 
 
 @pytest.fixture(scope="module", autouse=True)

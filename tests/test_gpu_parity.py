@@ -13,8 +13,8 @@ from gpu_helpers import (assert_bitexact, fer_in_interval, llrs, make_code, qc, 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-ALL = ["flooding", "rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp"]
-DYN = ["rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp"]
+ALL = ["flooding", "rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp", "lmdrbp", "slmdrbp"]
+DYN = ["rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp", "lmdrbp", "slmdrbp"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -56,7 +56,7 @@ def test_int6_bitexact_check_intervals_and_ragged_budgets(schedule, ci, budget):
 @pytest.mark.parametrize("schedule,n_p", [("flooding", 0), ("rbp", 0), ("cirbp", 0),
                                           ("lmd-cirbp", 0), ("me-cirbp", 64),
                                           ("me-lmd-cirbp", 4), ("me-lmd-cirbp", 16),
-                                          ("me-lmd-cirbp", 64)])
+                                          ("me-lmd-cirbp", 64), ("lmdrbp", 0), ("slmdrbp", 0)])
 def test_int6_bitexact_wifi_n2304(schedule, n_p):
     spec = qc("wifi", 96)
     code = make_code(spec)
@@ -67,7 +67,7 @@ def test_int6_bitexact_wifi_n2304(schedule, n_p):
     assert_bitexact(g, o, schedule)
 
 
-@pytest.mark.parametrize("schedule", ["lmd-cirbp", "cirbp", "me-lmd-cirbp", "flooding"])
+@pytest.mark.parametrize("schedule", ["lmd-cirbp", "cirbp", "me-lmd-cirbp", "flooding", "lmdrbp", "slmdrbp"])
 def test_int6_bitexact_bg2_degree1_and_punctured(schedule):
     spec = qc("bg2", 16)
     code = make_code(spec)
@@ -109,7 +109,7 @@ def test_fp32_trace_prefix_and_fer_regular_n96(schedule):
     assert ok, info
 
 
-@pytest.mark.parametrize("schedule", ["rbp", "cirbp", "lmd-cirbp"])
+@pytest.mark.parametrize("schedule", ["rbp", "cirbp", "lmd-cirbp", "lmdrbp", "slmdrbp"])
 def test_fp32_llr_tolerance_before_first_near_tie(schedule):
     spec = regular96()
     code = make_code(spec)

@@ -106,6 +106,31 @@ def test_toy_fp_initial_state_and_first_cirbp_step(golden_dir):
         assert list(o["trace"][0]) == g[key], sch
 
 
+def test_toy_fp_lmdrbp(golden_dir):
+    # Algorithm 2: line 9's residual argmax over the refreshed checks, then line 10
+    # re-selects the check into n' (LMDRBP) or not (sLMDRBP); hand-derived traces
+    g = _golden(golden_dir)
+    lam = np.array([[_ev(x) for x in g["fp"]["lam"]]])
+    for sch, key in [("lmdrbp", "lmdrbp_trace"), ("slmdrbp", "slmdrbp_trace")]:
+        o = oracle.decode(TOY_CHK, TOY_VAR, 2, 4, llr=lam, schedule=sch, max_updates=2,
+                          check_interval=0, want_trace=True)
+        assert list(o["trace"][0]) == g["fp"][key], sch
+    # degree-1 rule of Sec. 5.A (VN 0 and VN 3 have one check each)
+    d1 = g["fp_degree1"]
+    lam = np.array([[_ev(x) for x in d1["lam"]]])
+    o = oracle.decode(TOY_CHK, TOY_VAR, 2, 4, llr=lam, schedule="rbp", max_updates=0,
+                      check_interval=0, want_state=True)
+    np.testing.assert_allclose(o["state"]["P"][0], [_ev(x) for x in d1["init_P"]], rtol=0, atol=1e-13)
+    for sch, key in [("lmdrbp", "lmdrbp_trace"), ("slmdrbp", "slmdrbp_trace")]:
+        o = oracle.decode(TOY_CHK, TOY_VAR, 2, 4, llr=lam, schedule=sch, max_updates=3,
+                          check_interval=0, want_trace=True)
+        assert list(o["trace"][0]) == d1[key], sch
+        o = oracle.decode(TOY_CHK, TOY_VAR, 2, 4, llr=lam, schedule=sch, max_updates=2,
+                          check_interval=0, want_state=True)
+        np.testing.assert_allclose(o["state"]["P"][0], [_ev(x) for x in d1["P_after_step2"]],
+                                   rtol=0, atol=1e-13)
+
+
 def test_toy_fp_flooding_first_iteration_equals_precompute(golden_dir):
     # P6: one flooding iteration sends exactly the precomputed messages of eq. (2)
     g = _golden(golden_dir)["fp"]
@@ -267,7 +292,8 @@ def test_bp_never_beats_ml_on_tiny_code():
 # P4: invariants -- incremental == definitional, Table I counts, budgets
 
 
-@pytest.mark.parametrize("schedule", ["rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp"])
+@pytest.mark.parametrize("schedule", ["rbp", "cirbp", "lmd-cirbp", "me-cirbp", "me-lmd-cirbp", "lmdrbp",
+                                      "slmdrbp"])
 @pytest.mark.parametrize("arith", ["fp", "int"])
 def test_incremental_refresh_equals_definition(schedule, arith):
     c, v, m = wl.regular_code(48, 3, 6, 2)
