@@ -55,6 +55,8 @@ def parse():
                     help="run only the mixed-lifting queue comparison and print its JSON")
     ap.add_argument("--large-frames", type=int, default=304,
                     help="frames per point of the 26,112-bit BG1-shaped comparison (extras)")
+    ap.add_argument("--wbp-only", action="store_true",
+                    help="run only the weighted-BP forward/adjoint timing and print its JSON")
     ap.add_argument("--large-only", action="store_true",
                     help="run only the BG1-shaped cluster / global-memory comparison and print its JSON")
     return ap.parse_args()
@@ -503,6 +505,7 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
         res["queue_mixed_bg2"] = run_queue_mixed(args, L, device)
     if args.large_frames > 0:
         res["large_bg1_z384"] = run_large_bg1(args, L, device)
+    res["weighted_bp_config4"] = run_wbp_config4(args, L, device)
     return res
 
 
@@ -707,6 +710,49 @@ def run_large_bg1(args, L, device, frames=None, reps=2, points=None):
     return res
 
 
+def run_wbp_config4(args, L, device, frames=4096, reps=2):
+    """Weighted BP and its adjoint (12x24 protograph, Z=24: n=576), T = 8E
+    updates of an LMD-CIRBP schedule recorded at 2.0 dB, 4,096 frames: time of
+    the forward replay and of the adjoint (CUDA events), BCE loss."""
+    import torch
+    from paper_2102_11089_gb300 import workloads as wl
+    from paper_2102_11089_gb300.wbp import bce_all_zero, record_schedule, weighted_bp
+    d = wl.wifi_like(2, 24)
+    code = L.Code.from_protograph(d.shifts(24), 24, d.info_cols * 24, d.punct_cols)
+    eb = torch.full((frames,), 2.0, dtype=torch.float32, device=device)
+    llr, _ = L.awgn_llr(code, eb, seed=2021)
+    T = 8 * code.E
+    trace, _ = record_schedule(code, llr, T)
+    w = torch.ones(T, device=device, requires_grad=True)
+    x = llr.requires_grad_(False)
+
+    def fwd():
+        return weighted_bp(code, x, trace, w)
+
+    out = fwd()
+    loss = bce_all_zero(out)
+    loss.backward()
+    torch.cuda.synchronize()
+    tf, tb = [], []
+    for _ in range(reps):
+        w.grad = None
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        out = fwd()
+        b.record()
+        loss = bce_all_zero(out)
+        loss.backward()
+        c.record()
+        torch.cuda.synchronize()
+        tf.append(a.elapsed_time(b))
+        tb.append(b.elapsed_time(c))
+    upd = frames * T
+    return {"workload": "wifi-like 12x24, Z=24 (n=576), T=8E LMD-CIRBP schedule, 2.0 dB", "frames": frames,
+            "T": T, "forward_ms": min(tf), "backward_ms": min(tb), "loss": float(loss.detach()),
+            "forward_updates_per_s": upd / (min(tf) * 1e-3), "backward_updates_per_s": upd / (min(tb) * 1e-3),
+            "grad_norm": float(w.grad.norm())}
+
+
 def run_decode_only(args):
     import torch
     import __graft_entry__
@@ -738,6 +784,13 @@ def main():
         __graft_entry__.build()
         import paper_2102_11089_gb300 as L
         print(json.dumps(run_queue_mixed(args, L, torch.device("cuda", 0), reps=args.reps)))
+        return
+    if args.wbp_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2102_11089_gb300 as L
+        print(json.dumps(run_wbp_config4(args, L, torch.device("cuda", 0), reps=args.reps)))
         return
     if args.large_only:
         import torch

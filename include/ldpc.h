@@ -277,6 +277,43 @@ ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t *code, const void *llr, int6
                                   const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
                                   uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);
 
+/* Weighted BP along a recorded schedule, and its adjoint.  Not a step of the
+ * paper: the differentiable decoder built on its schedules.  A decode with
+ * `trace` records the edge committed at each update; the weighted decoder
+ * replays that schedule in FP32 with one weight per update: update t commits
+ * C[e_t] <- w[t] * P_t, P_t the C2V of eq. (2) (inputs and result clipped to
+ * +-llr_clip) from the state before the update, and returns
+ * L_n = lambda_n + sum_{m in M(n)} C[m->n] (eq. 3).  With unit weights this is
+ * the decoder's own message passing; the selection itself is not replayed.
+ * llr       : device float[batch][n_vars] channel LLRs
+ * trace     : device int32[batch][T] edge ids (rows of an ldpc_decode trace)
+ * counts    : device int64[batch] updates to replay per frame (<= T), or NULL (T)
+ * weights   : device float[T]
+ * llr_out   : device float[batch][n_vars] final L, or NULL
+ * c_out     : device float[batch][n_edges] final C2V state, or NULL
+ * tape      : device float[batch][T] value each update overwrote, or NULL
+ * Frame state lives in shared memory (one warp per frame).  Errors:
+ * INVALID_ARG, UNSUPPORTED (check degree > 32, or a frame's state larger than
+ * one CTA's shared memory), CUDA.  A trace entry outside [0, n_edges) stops
+ * that frame and makes the next ldpc_sync return LDPC_ERR_INVALID_ARG. */
+ldpc_status_t ldpc_wbp_forward(const ldpc_code_t *code, const float *llr, int64_t batch, const int32_t *trace,
+                               const int64_t *counts, int64_t T, const float *weights, float llr_clip,
+                               float *llr_out, float *c_out, float *tape, void *cuda_stream);
+
+/* Adjoint of ldpc_wbp_forward for a loss of the final LLRs: walks the updates
+ * backwards from the forward's final state, restoring each overwritten C2V
+ * value from the tape (no recomputation).
+ * c_final, tape : the forward's c_out and tape (device)
+ * dL        : device float[batch][n_vars] dloss/dL
+ * dw_frames : device float[batch][T] dloss/dw[t] per frame (required)
+ * dw        : device float[T] the same summed over frames, or NULL
+ * dllr      : device float[batch][n_vars] dloss/dllr, or NULL
+ * Same other arguments and errors as ldpc_wbp_forward. */
+ldpc_status_t ldpc_wbp_backward(const ldpc_code_t *code, const float *llr, int64_t batch, const int32_t *trace,
+                                const int64_t *counts, int64_t T, const float *weights, float llr_clip,
+                                const float *c_final, const float *tape, const float *dL, float *dw_frames,
+                                float *dw, float *dllr, void *cuda_stream);
+
 /* Wait for `cuda_stream` and return the device status accumulated by decode
  * calls on the current device since the previous ldpc_sync (the status word
  * is then cleared): LDPC_OK, LDPC_ERR_NONFINITE_LLR, LDPC_ERR_TIMEOUT,

@@ -79,6 +79,9 @@ def _lib():
                                    ctypes.c_int64, P, P]
             h.orc_qc_lift.restype = ctypes.c_int64
             h.orc_qc_lift.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P]
+            h.orc_wbp.restype = ctypes.c_int
+            h.orc_wbp.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int64,
+                                  P, P, ctypes.c_int64, P, ctypes.c_double, P, P, P, P, ctypes.c_int]
             h.orc_counters_count.restype = ctypes.c_int
             _handle = h
     return _handle
@@ -120,6 +123,36 @@ def qc_lift(base: np.ndarray, Z: int):
     var = np.zeros(e, dtype=np.int32)
     _lib().orc_qc_lift(_ptr(b), rows, cols, Z, _ptr(chk), _ptr(var))
     return chk, var
+
+
+def wbp(check_idx, var_idx, n_checks: int, n_vars: int, llr, trace, w, *, counts=None, llr_clip=25.0,
+        dL=None, threads=1):
+    """Weighted BP along recorded schedules (FP64): update t commits
+    w[t] * (clipped eq. 2 C2V) on edge trace[b, t].  Returns the final LLRs
+    [batch, N]; with dL (dloss/dL) also (dloss/dw per frame [batch, T],
+    dloss/dllr [batch, N]) by the adjoint."""
+    chk = np.ascontiguousarray(check_idx, dtype=np.int32)
+    var = np.ascontiguousarray(var_idx, dtype=np.int32)
+    lam = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float64)
+    tr = np.ascontiguousarray(np.atleast_2d(trace), dtype=np.int32)
+    wt = np.ascontiguousarray(w, dtype=np.float64)
+    B, T = tr.shape
+    assert lam.shape == (B, n_vars) and wt.shape == (T,)
+    cnt = None if counts is None else np.ascontiguousarray(counts, dtype=np.int64)
+    L = np.zeros((B, n_vars))
+    dw = dl = None
+    dLa = None
+    if dL is not None:
+        dLa = np.ascontiguousarray(np.atleast_2d(dL), dtype=np.float64)
+        dw = np.zeros((B, T))
+        dl = np.zeros((B, n_vars))
+    rc = _lib().orc_wbp(_ptr(chk), _ptr(var), len(chk), n_checks, n_vars, _ptr(lam), B, _ptr(tr),
+                        None if cnt is None else _ptr(cnt), T, _ptr(wt), llr_clip, _ptr(L),
+                        None if dLa is None else _ptr(dLa), None if dw is None else _ptr(dw),
+                        None if dl is None else _ptr(dl), threads)
+    if rc != 0:
+        raise RuntimeError(f"orc_wbp failed: {rc}")
+    return L if dL is None else (L, dw, dl)
 
 
 def alg4(D, in_set, n_g: int, n_p: int, arith: int = FP, seed: int = 0, frame: int = 0,

@@ -967,6 +967,146 @@ int orc_decode(const int32_t *chk, const int32_t *var, int64_t E, int32_t M, int
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Weighted BP along a recorded schedule, and its adjoint (not in the paper:  */
+/* the differentiable decoder built on it).  Update t of a frame commits edge */
+/* e_t = trace[t] as C[e_t] <- w[t] * P_t, where P_t is the clipped           */
+/* sum-product C2V of eq. (2) from the state before the update; the final    */
+/* L_n = lambda_n + sum C (eq. 3).  The adjoint runs the updates backwards,   */
+/* restoring each overwritten C[e_t] from the tape the forward kept.         */
+
+typedef struct {
+    const og_t *g;
+    const double *llr, *w, *dL;
+    const int32_t *trace;
+    const int64_t *counts;
+    int64_t T, b0, b1;
+    double clip;
+    double *L_out, *dw_out, *dllr_out;
+    int rc;
+} wjob_t;
+
+/* eq. (1) from the state C */
+static double w_v2c(const og_t *g, const double *lam, const double *C, int e) {
+    int n = g->e_vn[e];
+    double v = lam[n];
+    for (int k = g->vn_ptr[n]; k < g->vn_ptr[n + 1]; k++)
+        if (g->vn_e[k] != e) v += C[g->vn_e[k]];
+    return v;
+}
+
+static void *wjob_run(void *arg) {
+    wjob_t *J = (wjob_t *)arg;
+    const og_t *g = J->g;
+    double *C = (double *)malloc(sizeof(double) * (size_t)g->E);
+    double *Cb = (double *)malloc(sizeof(double) * (size_t)g->E);
+    double *tape = (double *)malloc(sizeof(double) * (size_t)(J->T > 0 ? J->T : 1));
+    double *u = (double *)malloc(sizeof(double) * (size_t)g->E);
+    double *th = (double *)malloc(sizeof(double) * (size_t)g->E);
+    if (!C || !Cb || !tape || !u || !th) { J->rc = ORC_ERR_NOMEM; goto done; }
+    for (int64_t b = J->b0; b < J->b1; b++) {
+        const double *lam = J->llr + b * g->N;
+        const int32_t *tr = J->trace + b * J->T;
+        int64_t cnt = J->counts ? J->counts[b] : J->T;
+        if (cnt > J->T) cnt = J->T;
+        for (int e = 0; e < g->E; e++) C[e] = 0.0;
+        for (int64_t t = 0; t < cnt; t++) { /* forward */
+            int e = tr[t], m = g->e_cn[e];
+            double prod = 1.0;
+            for (int e2 = g->cn_ptr[m]; e2 < g->cn_ptr[m + 1]; e2++) {
+                if (e2 == e) continue;
+                prod *= tanh(clampd(w_v2c(g, lam, C, e2), -J->clip, J->clip) / 2.0);
+            }
+            tape[t] = C[e];
+            C[e] = J->w[t] * clampd(2.0 * atanh(prod), -J->clip, J->clip);
+        }
+        for (int n = 0; n < g->N; n++) {
+            double s = lam[n];
+            for (int k = g->vn_ptr[n]; k < g->vn_ptr[n + 1]; k++) s += C[g->vn_e[k]];
+            if (J->L_out) J->L_out[b * g->N + n] = s;
+        }
+        if (!J->dL) continue;
+        /* adjoint: dloss/dC[e] = dloss/dL of its variable; dloss/dlambda likewise */
+        const double *dL = J->dL + b * g->N;
+        double *dw = J->dw_out ? J->dw_out + b * J->T : NULL;
+        double *dlam = J->dllr_out ? J->dllr_out + b * g->N : NULL;
+        for (int e = 0; e < g->E; e++) Cb[e] = dL[g->e_vn[e]];
+        if (dlam) for (int n = 0; n < g->N; n++) dlam[n] = dL[n];
+        if (dw) for (int64_t t = 0; t < J->T; t++) dw[t] = 0.0;
+        for (int64_t t = cnt - 1; t >= 0; t--) {
+            int e = tr[t], m = g->e_cn[e];
+            C[e] = tape[t]; /* the state before update t */
+            double prod = 1.0;
+            for (int e2 = g->cn_ptr[m]; e2 < g->cn_ptr[m + 1]; e2++) {
+                if (e2 == e) continue;
+                u[e2] = w_v2c(g, lam, C, e2);
+                th[e2] = tanh(clampd(u[e2], -J->clip, J->clip) / 2.0);
+                prod *= th[e2];
+            }
+            double Praw = 2.0 * atanh(prod);
+            double P = clampd(Praw, -J->clip, J->clip);
+            double a = Cb[e];
+            Cb[e] = 0.0; /* C[e] before the update does not reach the result */
+            if (dw) dw[t] += a * P;
+            double Pb = a * J->w[t];
+            if (fabs(Praw) >= J->clip || Pb == 0.0) continue;
+            /* dP/du_k = (1 - t_k^2) prod_{i != k} t_i / (1 - prod^2) for |u_k| < clip */
+            for (int e2 = g->cn_ptr[m]; e2 < g->cn_ptr[m + 1]; e2++) {
+                if (e2 == e || fabs(u[e2]) >= J->clip) continue;
+                double others = 1.0;
+                for (int e3 = g->cn_ptr[m]; e3 < g->cn_ptr[m + 1]; e3++)
+                    if (e3 != e && e3 != e2) others *= th[e3];
+                double ub = Pb * (1.0 - th[e2] * th[e2]) * others / (1.0 - prod * prod);
+                /* u = lambda_n + sum_{e3 in M(n)\e2} C[e3] */
+                int n = g->e_vn[e2];
+                if (dlam) dlam[n] += ub;
+                for (int k = g->vn_ptr[n]; k < g->vn_ptr[n + 1]; k++)
+                    if (g->vn_e[k] != e2) Cb[g->vn_e[k]] += ub;
+            }
+        }
+    }
+done:
+    free(C); free(Cb); free(tape); free(u); free(th);
+    return NULL;
+}
+
+/* Weighted BP of `batch` frames along `trace` ([batch][T] edge ids, the      */
+/* first counts[b] of each row used; counts NULL: all T), weights w[T], FP64. */
+/* Writes L_out [batch][N] (may be NULL); with dL (dloss/dL, [batch][N]) also */
+/* dw_out [batch][T] and dllr_out [batch][N] (either may be NULL).            */
+int orc_wbp(const int32_t *chk, const int32_t *var, int64_t E, int32_t M, int32_t N, const double *llr,
+            int64_t batch, const int32_t *trace, const int64_t *counts, int64_t T, const double *w,
+            double clip, double *L_out, const double *dL, double *dw_out, double *dllr_out, int n_threads) {
+    if (!llr || !trace || !w || batch < 0 || T < 0 || !(clip > 0.0)) return ORC_ERR_ARG;
+    og_t g;
+    int rc = og_build(&g, chk, var, E, M, N);
+    if (rc) return rc;
+    for (int64_t i = 0; i < batch * T; i++) {
+        int64_t b = i / (T > 0 ? T : 1), t = i % (T > 0 ? T : 1);
+        int64_t cnt = counts ? counts[b] : T;
+        if (t < cnt && (trace[i] < 0 || trace[i] >= g.E)) { og_free(&g); return ORC_ERR_RANGE; }
+    }
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > batch) n_threads = batch > 0 ? (int)batch : 1;
+    wjob_t *jobs = (wjob_t *)calloc((size_t)n_threads, sizeof(wjob_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; t++) {
+        wjob_t *J = &jobs[t];
+        J->g = &g; J->llr = llr; J->w = w; J->dL = dL; J->trace = trace; J->counts = counts;
+        J->T = T; J->clip = clip; J->L_out = L_out; J->dw_out = dw_out; J->dllr_out = dllr_out;
+        J->b0 = batch * t / n_threads; J->b1 = batch * (t + 1) / n_threads;
+    }
+    if (n_threads == 1) wjob_run(&jobs[0]);
+    else {
+        for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, wjob_run, &jobs[t]);
+        for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+    }
+    for (int t = 0; t < n_threads; t++) if (jobs[t].rc) rc = jobs[t].rc;
+    free(jobs); free(th);
+    og_free(&g);
+    return rc;
+}
+
 /* Algorithm 4 alone, for unit tests: D values of all N VNs, membership of S, */
 /* returns |P| and writes P ascending.                                        */
 int orc_alg4(const double *D, const uint8_t *inS, int32_t N, int32_t arith, int32_t n_g, int32_t n_p,

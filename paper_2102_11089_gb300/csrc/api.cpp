@@ -754,6 +754,82 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
   return LDPC_OK;
 }
 
+namespace {
+// Shared checks of the weighted-BP entry points; sets up `a` on success.
+ldpc_status_t wbp_setup(const ldpc_code_t* code, const float* llr, int64_t batch, const int32_t* trace, int64_t T,
+                        const float* weights, float llr_clip, bool backward, ldpc::WbpArgs* a, int* fpc) {
+  if (!code) return fail(LDPC_ERR_INVALID_ARG, "code is required");
+  if (batch < 0 || T < 0) return fail(LDPC_ERR_INVALID_ARG, "negative batch or T");
+  if (!(llr_clip > 0.0f && llr_clip <= 1.0e4f)) return fail(LDPC_ERR_INVALID_ARG, "llr_clip outside (0, 1e4]");
+  if (batch > 0 && (!llr || (T > 0 && (!trace || !weights))))
+    return fail(LDPC_ERR_INVALID_ARG, "llr, trace and weights are required");
+  std::memset(a, 0, sizeof(*a));
+  if (batch == 0) return LDPC_OK;
+  const ldpc::GraphDesc* g;
+  ldpc_status_t st = ensure_device(const_cast<ldpc_code_t*>(code), &g, nullptr);
+  if (st) return st;
+  if (g->dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint32_t* status;
+  st = device_status_word(dev, &status);
+  if (st) return st;
+  a->g = *g;
+  a->llr = llr;
+  a->batch = batch;
+  a->trace = trace;
+  a->T = T;
+  a->w = weights;
+  a->clip = llr_clip;
+  a->status = status;
+  a->graph_smem = ldpc::graph_smem_bytes(*g);
+  a->frame_bytes = ldpc::wbp_state_bytes(*g, backward);
+  const int64_t room = (int64_t)max_optin_smem() - a->graph_smem;
+  const int64_t f = std::min<int64_t>(8, std::min<int64_t>(batch, room / a->frame_bytes));
+  if (f < 1) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
+  *fpc = (int)f;
+  return LDPC_OK;
+}
+}  // namespace
+
+ldpc_status_t ldpc_wbp_forward(const ldpc_code_t* code, const float* llr, int64_t batch, const int32_t* trace,
+                               const int64_t* counts, int64_t T, const float* weights, float llr_clip,
+                               float* llr_out, float* c_out, float* tape, void* cuda_stream) {
+  ldpc::WbpArgs a;
+  int fpc = 0;
+  ldpc_status_t st = wbp_setup(code, llr, batch, trace, T, weights, llr_clip, false, &a, &fpc);
+  if (st || batch == 0) return st;
+  a.counts = counts;
+  a.llr_out = llr_out;
+  a.c_out = c_out;
+  a.tape = tape;
+  const cudaError_t e = ldpc::launch_wbp(a, false, fpc, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "weighted BP forward");
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_wbp_backward(const ldpc_code_t* code, const float* llr, int64_t batch, const int32_t* trace,
+                                const int64_t* counts, int64_t T, const float* weights, float llr_clip,
+                                const float* c_final, const float* tape, const float* dL, float* dw_frames,
+                                float* dw, float* dllr, void* cuda_stream) {
+  if (batch > 0 && (!c_final || !dL || !dw_frames || (T > 0 && !tape)))
+    return fail(LDPC_ERR_INVALID_ARG, "c_final, tape, dL and dw_frames are required");
+  ldpc::WbpArgs a;
+  int fpc = 0;
+  ldpc_status_t st = wbp_setup(code, llr, batch, trace, T, weights, llr_clip, true, &a, &fpc);
+  if (st || batch == 0) return st;
+  a.counts = counts;
+  a.c_in = c_final;
+  a.tape_in = tape;
+  a.dL = dL;
+  a.dw_frames = dw_frames;
+  a.dw = dw;
+  a.dllr = dllr;
+  const cudaError_t e = ldpc::launch_wbp(a, true, fpc, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "weighted BP backward");
+  return LDPC_OK;
+}
+
 ldpc_status_t ldpc_sync(void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -770,7 +846,8 @@ ldpc_status_t ldpc_sync(void* cuda_stream) {
     if (e != cudaSuccess) return cuda_fail(e, "clear status");
   }
   if (v & 2u) return fail(LDPC_ERR_TIMEOUT, "a bounded device wait gave up");
-  if (v & 4u) return fail(LDPC_ERR_INVALID_ARG, "a queue item named a code outside its call's code list");
+  if (v & 4u) return fail(LDPC_ERR_INVALID_ARG, "a queue item named a code outside its call's code list, "
+                                               "or a weighted-BP trace entry is not an edge id");
   if (v & 1u) return fail(LDPC_ERR_NONFINITE_LLR, "a decode saw a non-finite or out-of-range LLR");
   return LDPC_OK;
 }

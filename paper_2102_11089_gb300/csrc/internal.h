@@ -191,6 +191,32 @@ struct QueueArgs {
   int32_t smem_state_bytes;  // frame state kept in shared memory when it fits this, else global
 };
 
+// Weighted BP along a recorded schedule (decode_wbp.cu).
+struct WbpArgs {
+  GraphDesc g;
+  const float* llr;      // [batch][N]
+  int64_t batch;
+  const int32_t* trace;  // [batch][T] committed edge ids
+  const int64_t* counts; // [batch] updates used per frame, or null (all T)
+  int64_t T;
+  const float* w;        // [T] weight of update t
+  float clip;
+  float* llr_out;        // forward: [batch][N] final LLRs, or null
+  float* c_out;          // forward: [batch][E] final C2V state, or null
+  float* tape;           // forward: [batch][T] overwritten C2V values, or null
+  const float* c_in;     // backward: the forward's final C2V state
+  const float* tape_in;  // backward: the forward's tape
+  const float* dL;       // backward: [batch][N] dloss/dL
+  float* dw_frames;      // backward: [batch][T] dloss/dw per frame
+  float* dw;             // backward: [T] summed over frames, or null
+  float* dllr;           // backward: [batch][N] dloss/dllr, or null
+  uint32_t* status;      // bit 2: a trace entry is not an edge id
+  int32_t graph_smem;
+  int32_t frame_bytes;
+};
+int wbp_state_bytes(const GraphDesc& g, bool backward);
+cudaError_t launch_wbp(const WbpArgs& a, bool backward, int frames_per_cta, cudaStream_t s);
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int threads, int grid, size_t smem,
                             cudaStream_t s);
