@@ -506,6 +506,15 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
     if args.large_frames > 0:
         res["large_bg1_z384"] = run_large_bg1(args, L, device)
     res["weighted_bp_config4"] = run_wbp_config4(args, L, device)
+    # Properties 1 and 2 (Sec. 3.A) on flooding: empirical J(gamma), F(gamma) at
+    # gamma = 0, 0.1, ..., 0.9 for iterations 0-2 (analogue of the paper's Fig. 1b)
+    from paper_2102_11089_gb300.ci_stats import flooding_counts, j_and_f
+    cnt = flooding_counts(code, x, 3, n_bins=10)
+    J, F = j_and_f(cnt)
+    clean = lambda a: [None if not np.isfinite(v) else float(v) for v in a]  # noqa: E731
+    res["ci_properties_flooding"] = {"frames": int(x.shape[0]), "gamma": [b / 10 for b in range(10)],
+                                     "J": [clean(J[k]) for k in range(3)], "F": [clean(F[k]) for k in range(3)],
+                                     "incorrect_per_iteration": [int(cnt[k][:, 1].sum()) for k in range(3)]}
     return res
 
 

@@ -314,6 +314,19 @@ ldpc_status_t ldpc_wbp_backward(const ldpc_code_t *code, const float *llr, int64
                                 const float *c_final, const float *tape, const float *dL, float *dw_frames,
                                 float *dw, float *dllr, void *cuda_stream);
 
+/* Counters of the CI metric's Properties 1 and 2 (Sec. 3.A), for the
+ * all-zero codeword: for each of `count` pairs (L, L~) -- a VN's current and
+ * precomputed total LLR, e.g. consecutive flooding iterations -- bin
+ * D = |p0(L) - p0(L~)| (eq. 8) by b = min(floor(D * n_bins), n_bins - 1) and
+ * count per bin: [0] L >= 0 (decision correct), [1] L < 0, [2] L < 0 and
+ * L~ >= L, [3] L < 0 and L~ < L.  Cumulated from the top bin, [0]/[1] is the
+ * empirical J(gamma) and [2]/[3] F(gamma) at gamma = b / n_bins.
+ * llr_now, llr_pre : device float[count]
+ * counts           : device uint64[n_bins][4], overwritten (stream-ordered)
+ * Errors: INVALID_ARG (n_bins outside 1..1024), CUDA. */
+ldpc_status_t ldpc_ci_stats(const float *llr_now, const float *llr_pre, int64_t count, int32_t n_bins,
+                            uint64_t *counts, void *cuda_stream);
+
 /* Wait for `cuda_stream` and return the device status accumulated by decode
  * calls on the current device since the previous ldpc_sync (the status word
  * is then cleared): LDPC_OK, LDPC_ERR_NONFINITE_LLR, LDPC_ERR_TIMEOUT,

@@ -155,6 +155,27 @@ def wbp(check_idx, var_idx, n_checks: int, n_vars: int, llr, trace, w, *, counts
     return L if dL is None else (L, dw, dl)
 
 
+def ci_counts(L, Lt, n_bins: int) -> np.ndarray:
+    """Counters of Properties 1 and 2 (Sec. 3.A) for the all-zero codeword, in
+    FP64 from the definitions: D = |p0(L) - p0(L~)| (eq. 8), p0(x) = 1/(1 + e^-x),
+    bin min(floor(D n_bins), n_bins - 1); per bin [#(L >= 0), #(L < 0),
+    #(L < 0 and p0(L~) >= p0(L)), #(L < 0 and p0(L~) < p0(L))]."""
+    L = np.asarray(L, dtype=np.float64).ravel()
+    Lt = np.asarray(Lt, dtype=np.float64).ravel()
+    p0 = 0.5 + 0.5 * np.tanh(L / 2.0)     # = 1 / (1 + e^-L), exact form
+    p0t = 0.5 + 0.5 * np.tanh(Lt / 2.0)
+    D = np.abs(np.tanh(L / 2.0) - np.tanh(Lt / 2.0)) / 2.0
+    b = np.minimum(np.floor(D * n_bins).astype(np.int64), n_bins - 1)
+    out = np.zeros((n_bins, 4), dtype=np.int64)
+    wrong = L < 0
+    np.add.at(out[:, 0], b[~wrong], 1)
+    np.add.at(out[:, 1], b[wrong], 1)
+    up = wrong & (p0t >= p0)
+    np.add.at(out[:, 2], b[up], 1)
+    np.add.at(out[:, 3], b[wrong & ~up], 1)
+    return out
+
+
 def alg4(D, in_set, n_g: int, n_p: int, arith: int = FP, seed: int = 0, frame: int = 0,
          step: int = 0):
     D = np.ascontiguousarray(D, dtype=np.float64)

@@ -89,6 +89,7 @@ def _load():
             ("ldpc_decode_noalloc", [P, P, I64, P, P, P, P, P, P, P]),
             ("ldpc_decode_queue", [P, I32, P, I64, P, P, P, P, P, I32, P]),
             ("ldpc_wbp_forward", [P, P, I64, P, P, I64, P, ctypes.c_float, P, P, P, P]),
+            ("ldpc_ci_stats", [P, P, I64, I32, P, P]),
             ("ldpc_wbp_backward", [P, P, I64, P, P, I64, P, ctypes.c_float, P, P, P, P, P, P, P]),
             ("ldpc_sync", [P]),
         ]:

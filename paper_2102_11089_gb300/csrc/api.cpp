@@ -830,6 +830,19 @@ ldpc_status_t ldpc_wbp_backward(const ldpc_code_t* code, const float* llr, int64
   return LDPC_OK;
 }
 
+ldpc_status_t ldpc_ci_stats(const float* llr_now, const float* llr_pre, int64_t count, int32_t n_bins,
+                            uint64_t* counts, void* cuda_stream) {
+  if (count < 0 || n_bins < 1 || n_bins > 1024) return fail(LDPC_ERR_INVALID_ARG, "count >= 0 and 1 <= n_bins <= 1024");
+  if (!counts || (count > 0 && (!llr_now || !llr_pre))) return fail(LDPC_ERR_INVALID_ARG, "NULL buffer");
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cudaError_t e = ldpc::launch_ci_stats(llr_now, llr_pre, count, n_bins, (unsigned long long*)counts, sms,
+                                              (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ci_stats");
+  return LDPC_OK;
+}
+
 ldpc_status_t ldpc_sync(void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");

@@ -217,6 +217,9 @@ struct WbpArgs {
 int wbp_state_bytes(const GraphDesc& g, bool backward);
 cudaError_t launch_wbp(const WbpArgs& a, bool backward, int frames_per_cta, cudaStream_t s);
 
+cudaError_t launch_ci_stats(const float* La, const float* Lb, int64_t count, int n_bins, unsigned long long* out,
+                            int sms, cudaStream_t s);
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int threads, int grid, size_t smem,
                             cudaStream_t s);

@@ -187,3 +187,12 @@ def test_queue_validation_needs_no_gpu(lib):
     r = L.make_params("me-cirbp", tune=0x100)
     assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
     assert L.WORK_ITEM_DTYPE.itemsize == 40
+
+
+def test_ci_stats_validation_needs_no_gpu(lib):
+    null = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(64)
+    for nb in (0, 1025):
+        assert lib.ldpc_ci_stats(dummy, dummy, 10, nb, dummy, null) == -1
+    assert lib.ldpc_ci_stats(null, dummy, 10, 8, dummy, null) == -1
+    assert lib.ldpc_ci_stats(dummy, dummy, -1, 8, dummy, null) == -1
