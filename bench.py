@@ -509,10 +509,10 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
     # Properties 1 and 2 (Sec. 3.A) on flooding: empirical J(gamma), F(gamma) at
     # gamma = 0, 0.1, ..., 0.9 for iterations 0-2 (analogue of the paper's Fig. 1b)
     from paper_2102_11089_gb300.ci_stats import flooding_counts, j_and_f
-    cnt = flooding_counts(code, x, 3, n_bins=10)
+    cnt = flooding_counts(code, llr, 3, n_bins=10)
     J, F = j_and_f(cnt)
     clean = lambda a: [None if not np.isfinite(v) else float(v) for v in a]  # noqa: E731
-    res["ci_properties_flooding"] = {"frames": int(x.shape[0]), "gamma": [b / 10 for b in range(10)],
+    res["ci_properties_flooding"] = {"frames": int(llr.shape[0]), "gamma": [b / 10 for b in range(10)],
                                      "J": [clean(J[k]) for k in range(3)], "F": [clean(F[k]) for k in range(3)],
                                      "incorrect_per_iteration": [int(cnt[k][:, 1].sum()) for k in range(3)]}
     return res

@@ -190,6 +190,26 @@ ldpc_status_t ldpc_awgn_llr(const ldpc_code_t *code, const float *ebn0_db, int64
                             uint64_t seed, uint64_t frame_offset, float *llr, int8_t *qllr,
                             float q_step, void *cuda_stream);
 
+/* As ldpc_awgn_llr for arbitrary codewords: x = 1 - 2c for the bits c of
+ * `codewords` (device uint8[batch][n_vars], 0/1; NULL = the all-zero word). */
+ldpc_status_t ldpc_awgn_llr_codewords(const ldpc_code_t *code, const float *ebn0_db, int64_t batch,
+                                      uint64_t seed, uint64_t frame_offset, const uint8_t *codewords,
+                                      float *llr, int8_t *qllr, float q_step, void *cuda_stream);
+
+/* Systematic encoder (not a step of the paper's decoders: it lets the channel
+ * send codewords other than the all-zero word).  For codes built by
+ * ldpc_code_build_qc whose k_info is a whole number kb of block columns and
+ * whose parity part has the dual-diagonal shape of the IEEE 802.11 / 5G NR
+ * cores: first parity block column with shift s in rows 0 and c-1 and shift 0
+ * in one middle row, a shift-0 staircase over the next c-1 columns, then one
+ * identity column per remaining row.  codeword = info bits | parity bits.
+ * info      : device uint8[batch][k_info] (bit 0 of each byte)
+ * codewords : device uint8[batch][n_vars] (0/1)
+ * Errors: INVALID_ARG, UNSUPPORTED (other codes, more than 4096 protograph
+ * cells), NOMEM, CUDA. */
+ldpc_status_t ldpc_encode(const ldpc_code_t *code, const uint8_t *info, int64_t batch, uint8_t *codewords,
+                          void *cuda_stream);
+
 /* Decode `batch` independent frames.
  * llr       : device [batch][n_vars]; float for FP32, int8 in [-31, 31] for INT6
  * params    : host; schedule, arithmetic and budget (see ldpc_decode_params_t)

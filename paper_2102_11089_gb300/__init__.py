@@ -90,6 +90,8 @@ def _load():
             ("ldpc_decode_queue", [P, I32, P, I64, P, P, P, P, P, I32, P]),
             ("ldpc_wbp_forward", [P, P, I64, P, P, I64, P, ctypes.c_float, P, P, P, P]),
             ("ldpc_ci_stats", [P, P, I64, I32, P, P]),
+            ("ldpc_encode", [P, P, I64, P, P]),
+            ("ldpc_awgn_llr_codewords", [P, P, I64, U64, U64, P, P, P, ctypes.c_float, P]),
             ("ldpc_wbp_backward", [P, P, I64, P, P, I64, P, ctypes.c_float, P, P, P, P, P, P, P]),
             ("ldpc_sync", [P]),
         ]:
@@ -287,6 +289,33 @@ def awgn_llr(code: Code, ebn0_db, seed: int, frame_offset: int = 0, *, quantize=
                                  frame_offset, ctypes.c_void_p(out.data_ptr()),
                                  None if qout is None else ctypes.c_void_p(qout.data_ptr()),
                                  q_step, _stream_ptr(stream)))
+    return out, qout
+
+
+def encode(code: Code, info, stream=None):
+    """Codewords [batch, N] (uint8 0/1) of the info bits [batch, K] (uint8)."""
+    import torch
+    if not info.is_cuda or info.dtype != torch.uint8 or not info.is_contiguous():
+        raise ValueError("info must be a contiguous CUDA uint8 tensor")
+    B = info.shape[0]
+    cw = torch.empty((B, code.N), dtype=torch.uint8, device=info.device)
+    _check(_load().ldpc_encode(code._h, ctypes.c_void_p(info.data_ptr()), B, ctypes.c_void_p(cw.data_ptr()),
+                               _stream_ptr(stream)))
+    return cw
+
+
+def awgn_llr_codewords(code: Code, ebn0_db, codewords, seed: int, frame_offset: int = 0, *, quantize=False,
+                       q_step=0.5, stream=None):
+    """Channel LLRs of `codewords` ([batch, N] uint8, CUDA); as awgn_llr."""
+    import torch
+    B = ebn0_db.shape[0]
+    dev = ebn0_db.device
+    out = torch.empty((B, code.N), dtype=torch.float32, device=dev)
+    qout = torch.empty((B, code.N), dtype=torch.int8, device=dev) if quantize else None
+    _check(_load().ldpc_awgn_llr_codewords(code._h, ctypes.c_void_p(ebn0_db.data_ptr()), B, seed, frame_offset,
+                                           ctypes.c_void_p(codewords.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                           None if qout is None else ctypes.c_void_p(qout.data_ptr()), q_step,
+                                           _stream_ptr(stream)))
     return out, qout
 
 

@@ -63,6 +63,8 @@ struct ldpc_code {
   std::vector<uint8_t> punct;
   // protograph view (codes from ldpc_code_build_qc): see graph.cuh
   std::vector<int32_t> qc;  // rowbase | rowfirst | colfirst | rowblk | colblk
+  std::vector<int32_t> base;  // protograph shifts (codes from ldpc_code_build_qc)
+  int32_t base_rows = 0, base_cols = 0;
   int32_t qc_R = 0, qc_C = 0, qc_nnz = 0;
   uint32_t qc_zmul = 0, qc_zshift = 0;
   std::mutex mu;
@@ -419,7 +421,12 @@ ldpc_status_t ldpc_code_build_qc(const int32_t* base, int32_t rows, int32_t cols
       if (punct_cols[c]) std::fill(punct.begin() + (size_t)c * Z, punct.begin() + (size_t)(c + 1) * Z, 1);
   ldpc_status_t st = build_code(chk.data(), var.data(), (int64_t)chk.size(), rows * Z, cols * Z, punct.data(),
                                 k_info, Z, out);
-  if (st == LDPC_OK) build_qc_view(*out, base, rows, cols, Z);
+  if (st == LDPC_OK) {
+    build_qc_view(*out, base, rows, cols, Z);
+    (*out)->base.assign(base, base + (int64_t)rows * cols);
+    (*out)->base_rows = rows;
+    (*out)->base_cols = cols;
+  }
   return st;
 }
 
@@ -458,8 +465,9 @@ ldpc_status_t ldpc_code_edges(const ldpc_code_t* c, int32_t* check_out, int32_t*
   return LDPC_OK;
 }
 
-ldpc_status_t ldpc_awgn_llr(const ldpc_code_t* code, const float* ebn0_db, int64_t batch, uint64_t seed,
-                            uint64_t frame_offset, float* llr, int8_t* qllr, float q_step, void* cuda_stream) {
+ldpc_status_t ldpc_awgn_llr_codewords(const ldpc_code_t* code, const float* ebn0_db, int64_t batch, uint64_t seed,
+                                      uint64_t frame_offset, const uint8_t* codewords, float* llr, int8_t* qllr,
+                                      float q_step, void* cuda_stream) {
   if (!code) return fail(LDPC_ERR_INVALID_ARG, "code is NULL");
   if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
   if (batch == 0) return LDPC_OK;
@@ -472,9 +480,42 @@ ldpc_status_t ldpc_awgn_llr(const ldpc_code_t* code, const float* ebn0_db, int64
   const int32_t ntx = code->N - code->n_punct;
   if (ntx <= 0) return fail(LDPC_ERR_INVALID_ARG, "every VN is punctured");
   const float rate = (float)code->K / (float)ntx;
-  cudaError_t e = ldpc::launch_channel(g->N, punct, rate, ebn0_db, batch, seed, frame_offset, llr, qllr, q_step,
-                                       (cudaStream_t)cuda_stream);
+  cudaError_t e = ldpc::launch_channel(g->N, punct, codewords, rate, ebn0_db, batch, seed, frame_offset, llr, qllr,
+                                       q_step, (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "channel launch");
+  return LDPC_OK;
+}
+
+ldpc_status_t ldpc_awgn_llr(const ldpc_code_t* code, const float* ebn0_db, int64_t batch, uint64_t seed,
+                            uint64_t frame_offset, float* llr, int8_t* qllr, float q_step, void* cuda_stream) {
+  return ldpc_awgn_llr_codewords(code, ebn0_db, batch, seed, frame_offset, nullptr, llr, qllr, q_step, cuda_stream);
+}
+
+ldpc_status_t ldpc_encode(const ldpc_code_t* code, const uint8_t* info, int64_t batch, uint8_t* codewords,
+                          void* cuda_stream) {
+  if (!code) return fail(LDPC_ERR_INVALID_ARG, "code is NULL");
+  if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
+  if (code->base.empty()) return fail(LDPC_ERR_UNSUPPORTED, "encoding needs a code built by ldpc_code_build_qc");
+  ldpc::EncArgs* plan = new (std::nothrow) ldpc::EncArgs;
+  if (!plan) return fail(LDPC_ERR_NOMEM, "host allocation");
+  if (!ldpc::encode_plan(code->base.data(), code->base_rows, code->base_cols, code->Z, code->K, plan)) {
+    delete plan;
+    return fail(LDPC_ERR_UNSUPPORTED, "the parity part is not the dual-diagonal core + extension shape");
+  }
+  if (batch == 0) {
+    delete plan;
+    return LDPC_OK;
+  }
+  if (!info || !codewords) {
+    delete plan;
+    return fail(LDPC_ERR_INVALID_ARG, "info and codewords are required");
+  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cudaError_t e = ldpc::launch_encode(*plan, info, codewords, batch, sms, (cudaStream_t)cuda_stream);
+  delete plan;
+  if (e != cudaSuccess) return cuda_fail(e, "encode launch");
   return LDPC_OK;
 }
 

@@ -1,6 +1,6 @@
 // channel.cu -- BPSK / AWGN channel LLRs (Sec. 2.A and Sec. 5).
 //
-// All-zero codeword: x = +1, y = 1 + sigma w, N0/2 = sigma^2 with
+// Codeword bits c (all-zero unless given): x = 1 - 2c, y = x + sigma w, N0/2 = sigma^2 with
 // sigma^2 = 1 / (2 R 10^(EbN0/10)), LLR lambda = 2 y / sigma^2; punctured VNs
 // are not transmitted and get lambda = 0.  Gaussian samples come from
 // Box-Muller on Philox4x32-10 words (Salmon et al., SC'11): variable nodes
@@ -38,7 +38,7 @@ __device__ __forceinline__ float minus2_log_u(uint32_t x) {
 }
 
 __global__ void __launch_bounds__(256) awgn_kernel(int N, const uint8_t* __restrict__ punct,
-                                                   float rate, const float* __restrict__ ebn0,
+                                                   const uint8_t* __restrict__ cw, float rate, const float* __restrict__ ebn0,
                                                    int64_t batch, uint64_t seed, uint64_t frame_offset,
                                                    float* __restrict__ llr, int8_t* __restrict__ qllr,
                                                    float q_step) {
@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) awgn_kernel(int N, const uint8_t* __restr
       const int n = 4 * k + i;
       if (n >= N) break;
       const bool pn = punct != nullptr && punct[n];
-      const float lam = pn ? 0.0f : scale * (1.0f + sigma * z[i]);
+      const float x = (cw != nullptr && (cw[b * N + n] & 1u)) ? -1.0f : 1.0f;
+      const float lam = pn ? 0.0f : scale * (x + sigma * z[i]);
       llr[b * N + n] = lam;
       if (qllr) {
         const float q = fminf(31.0f, fmaxf(-31.0f, rintf(lam / q_step)));
@@ -81,8 +82,8 @@ __global__ void __launch_bounds__(256) awgn_kernel(int N, const uint8_t* __restr
 
 }  // namespace
 
-cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float* ebn0, int64_t batch,
-                           uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
+cudaError_t launch_channel(int N, const uint8_t* punct, const uint8_t* codewords, float rate, const float* ebn0,
+                           int64_t batch, uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
                            cudaStream_t s) {
   if (batch == 0) return cudaSuccess;
   const int64_t work = batch * (int64_t)((N + 3) / 4);
@@ -91,7 +92,7 @@ cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float*
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (work + 255) / 256;
   const int grid = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-  awgn_kernel<<<grid, 256, 0, s>>>(N, punct, rate, ebn0, batch, seed, frame_offset, llr, qllr, q_step);
+  awgn_kernel<<<grid, 256, 0, s>>>(N, punct, codewords, rate, ebn0, batch, seed, frame_offset, llr, qllr, q_step);
   return cudaGetLastError();
 }
 

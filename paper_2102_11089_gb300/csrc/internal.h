@@ -220,6 +220,18 @@ cudaError_t launch_wbp(const WbpArgs& a, bool backward, int frames_per_cta, cuda
 cudaError_t launch_ci_stats(const float* La, const float* Lb, int64_t count, int n_bins, unsigned long long* out,
                             int sms, cudaStream_t s);
 
+// Systematic encoder of dual-diagonal lifted codes (encode.cu).
+constexpr int kEncMaxBlocks = 4096;  // protograph cells
+constexpr int kEncMaxCore = 64;
+struct EncArgs {
+  int32_t Z, R, C;  // lifting, protograph rows and columns
+  int32_t kb;       // info block columns
+  int32_t c, x, s;  // core rows, middle row of the first parity column, its shift
+  int16_t B[kEncMaxBlocks];  // shifts, -1 for empty blocks (row-major R x C)
+};
+bool encode_plan(const int32_t* base, int R, int C, int Z, int K, EncArgs* out);
+cudaError_t launch_encode(const EncArgs& a, const uint8_t* info, uint8_t* cw, int64_t batch, int sms, cudaStream_t s);
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_me_queue(const QueueArgs& q, int arith, int sched, int threads, int grid, size_t smem,
                             cudaStream_t s);
@@ -234,8 +246,8 @@ cudaError_t launch_me_cluster(const DecodeArgs& a, int arith, int sched, int thr
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
 cudaError_t launch_flood(const DecodeArgs& a, int arith, cudaStream_t s);
 cudaError_t launch_me(const DecodeArgs& a, int arith, int sched, cudaStream_t s);
-cudaError_t launch_channel(int N, const uint8_t* punct, float rate, const float* ebn0, int64_t batch,
-                           uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
+cudaError_t launch_channel(int N, const uint8_t* punct, const uint8_t* codewords, float rate, const float* ebn0,
+                           int64_t batch, uint64_t seed, uint64_t frame_offset, float* llr, int8_t* qllr, float q_step,
                            cudaStream_t s);
 
 // Host-side view of a code handle (arrays owned by the handle).

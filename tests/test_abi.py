@@ -196,3 +196,17 @@ def test_ci_stats_validation_needs_no_gpu(lib):
         assert lib.ldpc_ci_stats(dummy, dummy, 10, nb, dummy, null) == -1
     assert lib.ldpc_ci_stats(null, dummy, 10, 8, dummy, null) == -1
     assert lib.ldpc_ci_stats(dummy, dummy, -1, 8, dummy, null) == -1
+
+
+def test_encode_plan_needs_no_gpu(lib):
+    null = ctypes.c_void_p()
+    for which, Z in [("wifi", 96), ("wifi", 24), ("bg2", 16), ("bg2", 384), ("bg1", 384)]:
+        d = wl.design(which)
+        code = L.Code.from_protograph(d.shifts(Z), Z, d.info_cols * Z, d.punct_cols)
+        assert lib.ldpc_encode(code._h, null, 0, null, null) == 0, (which, Z)  # plan accepted
+    c, v, m = wl.regular_code(96, 3, 6, 1)
+    tab = L.Code.from_edges(c, v, m, 96, 48)
+    assert lib.ldpc_encode(tab._h, null, 0, null, null) == -5  # no protograph
+    base = np.zeros((3, 6), np.int32)  # all-ones protograph: no dual-diagonal core
+    qc = L.Code.from_protograph(base, 4, 12)
+    assert lib.ldpc_encode(qc._h, null, 0, null, null) == -5
