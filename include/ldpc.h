@@ -118,7 +118,8 @@ typedef struct {
                                codes whose state fits two CTAs per SM, 1 = three,
                                2 = one, 3 = global memory only); bits 6-7 CTAs per
                                cluster of the cluster form (0 = smallest that fits,
-                               1 = 4, 2 = 8, 3 = 16); other bits 0                  */
+                               1 = 4, 2 = 8, 3 = 16); bit 8 single-edge state in
+                               global memory (as LDPC_FORM_GLOBAL); other bits 0    */
 } ldpc_decode_params_t;
 
 /* One frame of the work queue of ldpc_decode_queue. */
@@ -223,7 +224,8 @@ ldpc_status_t ldpc_encode(const ldpc_code_t *code, const uint8_t *info, int64_t 
  *             (INT6: the integer value)
  * Stops at a zero syndrome (checked per check_interval) or at the budget.
  * Execution form (params->form = LDPC_FORM_AUTO): frame state in shared
- * memory when it fits one CTA; else, for the multi-edge schedules and a batch
+ * memory when it fits one CTA (single-edge frames: when shared memory holds
+ * at least four per SM, else global memory); else, for the multi-edge schedules and a batch
  * of at most twice the resident clusters (SMs / cluster size), spread over the
  * shared memory of a thread-block cluster (the smallest of 2, 4, 8 or 16 CTAs
  * that holds it and can be resident); else global memory.  A cluster size in

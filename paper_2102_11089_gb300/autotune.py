@@ -4,8 +4,8 @@ The decode kernels take launch-shape hints in ``ldpc_decode_params_t.tune``:
 CTA size of the multi-edge kernels (bits 0-1), frames per CTA of the
 single-edge kernels (bits 2-3), for the work-queue form where frame state
 lives (bits 4-5: shared memory for codes that fit two, three or one CTA per
-SM, or global memory only) and the multi-edge cluster form with 4, 8 or 16
-CTAs per cluster (bits 6-7).  None of them changes a result; they only move
+SM, or global memory only), the multi-edge cluster form with 4, 8 or 16
+CTAs per cluster (bits 6-7) and single-edge state in global memory (bit 8).  None of them changes a result; they only move
 work between threads, CTAs and memories.
 
 The tuner runs a grid search over the hints that apply to a call on a
@@ -25,6 +25,7 @@ import threading
 from . import FLOODING, ME_CIRBP, ME_LMD_CIRBP, RBP, CIRBP, LMD_CIRBP  # noqa: F401
 
 CTA_256, CTA_512 = 1, 2
+GLOBAL_STATE = 1 << 8
 PLACE_HALF, PLACE_THIRD, PLACE_FULL, PLACE_GLOBAL = 0, 1, 2, 3
 
 
@@ -42,7 +43,8 @@ def candidates(entry: str, schedule: int) -> list[int]:
         return [CTA_256, CTA_512] + [CTA_512 | (cl << 6) for cl in (1, 2, 3)]
     if schedule == FLOODING:
         return [0]
-    return [fpc << 2 for fpc in (0, 1, 2, 3)]
+    # frames per CTA with state in shared memory, or state in global memory (bit 8)
+    return [fpc << 2 for fpc in (0, 1, 2, 3)] + [GLOBAL_STATE]
 
 
 def describe(tune: int) -> dict:
@@ -50,7 +52,8 @@ def describe(tune: int) -> dict:
     fpc = {0: "auto", 1: 2, 2: 4, 3: 8}[(tune >> 2) & 3]
     place = {0: "smem<=1/2 SM", 1: "smem<=1/3 SM", 2: "smem<=1 SM", 3: "global"}[(tune >> 4) & 3]
     cluster = {0: "auto", 1: 4, 2: 8, 3: 16}[(tune >> 6) & 3]
-    return {"cta_threads": cta, "frames_per_cta": fpc, "queue_state": place, "cluster_ctas": cluster}
+    return {"cta_threads": cta, "frames_per_cta": fpc, "queue_state": place, "cluster_ctas": cluster,
+            "single_edge_global_state": bool(tune & GLOBAL_STATE)}
 
 
 def cache_key(entry: str, device: str, codes, params) -> str:

@@ -535,7 +535,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (ldpc::is_multi_edge(p->schedule) && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 1024))
     return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 1024 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0xff) != 0 || (p->tune & 3) == 3)
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0x1ff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (p->form == LDPC_FORM_CLUSTER && !ldpc::is_multi_edge(p->schedule))
     return fail(LDPC_ERR_UNSUPPORTED, "the cluster form runs the multi-edge schedules");
@@ -608,9 +608,10 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   if (p->form == LDPC_FORM_SMEM && !fits) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
   // Cluster form (multi-edge): on request (LDPC_FORM_CLUSTER, or a cluster
   // size in tune bits 6-7), or for frames too large for one CTA when the batch
-  // is small: a cluster decodes a frame about three times sooner than a CTA
-  // with global-memory state but holds cs SMs, so with auto sizing it is taken
-  // while the batch is at most twice the resident clusters.  The smallest
+  // is small: a cluster decodes a frame as fast as a CTA with global-memory
+  // state, or up to several times faster (larger N_P, 6-bit), but holds cs SMs,
+  // so with auto sizing it is taken while the batch is at most twice the
+  // resident clusters.  The smallest
   // cluster (or the requested size) whose shared memory holds the state and
   // that can be resident; else the global-memory form.
   const int req = (p->tune >> 6) & 3;
@@ -636,7 +637,12 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     if (p->form == LDPC_FORM_CLUSTER) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds a resident cluster");
   }
   if ((int64_t)cta_fixed + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "working set exceeds shared memory");
-  const bool global_form = p->form == LDPC_FORM_GLOBAL || !fits;
+  // single-edge frames (a warp each) that shared memory holds fewer than four
+  // per SM run faster with their state in global memory and 32 warps per SM
+  // (FP32 WiFi-like code: 2.4-2.8x); tune bit 8 asks for it too
+  const bool se_few = ldpc::is_single_edge(p->schedule) && fits &&
+                      ((p->tune & 0x100) != 0 || (int64_t)228 * 1024 / ((int64_t)per + 1024) < 4);
+  const bool global_form = p->form == LDPC_FORM_GLOBAL || !fits || (p->form == LDPC_FORM_AUTO && se_few);
   void* scratch = nullptr;
   a.smem_per_frame = (int32_t)per;
   if (global_form) {
@@ -692,7 +698,7 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t* const* codes, int32_t n_codes
   if (p->arith != LDPC_FP32_SUMPRODUCT && p->arith != LDPC_INT6_MINSUM)
     return fail(LDPC_ERR_INVALID_ARG, "unknown arithmetic");
   if (p->check_interval < 0 || !(p->gamma >= 0.0 && p->gamma <= 1.0) || !(p->llr_clip > 0.0f && p->llr_clip <= 1.0e4f) ||
-      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0xff) != 0 || (p->tune & 3) == 3)
+      (p->arith == LDPC_INT6_MINSUM && !(p->q_step > 0.0f)) || (p->tune & ~0x1ff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad parameters");
   const bool me = p->schedule != LDPC_LMD_CIRBP;
   if (me && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255)) return fail(LDPC_ERR_INVALID_ARG, "n_p, n_g");

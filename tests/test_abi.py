@@ -129,7 +129,7 @@ def test_decode_validation_needs_no_gpu(lib):
     # batch 0 is a no-op
     assert lib.ldpc_decode(code._h, null, 0, ctypes.byref(p), null, null, null, null, null, null) == 0
     bad = [("schedule", 9), ("arith", 5), ("max_updates", -1), ("gamma", 1.5), ("llr_clip", 0.0), ("llr_clip", 2e4),
-           ("tune", 0x100), ("tune", 3), ("check_interval", -2)]
+           ("tune", 0x200), ("tune", 3), ("check_interval", -2)]
     for field, val in bad:
         q = L.make_params("lmd-cirbp", max_updates=10)
         setattr(q, field, val)
@@ -184,7 +184,7 @@ def test_queue_validation_needs_no_gpu(lib):
         assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -5
     r = L.make_params("me-cirbp", n_p=0)
     assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
-    r = L.make_params("me-cirbp", tune=0x100)
+    r = L.make_params("me-cirbp", tune=0x200)
     assert q(one, 1, dummy, 1, dummy, ctypes.byref(r), null, null, null, 1, null) == -1
     assert L.WORK_ITEM_DTYPE.itemsize == 40
 

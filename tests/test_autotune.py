@@ -19,7 +19,7 @@ def test_candidates_are_valid_hints(entry, schedule):
     c = at.candidates(entry, schedule)
     assert c and len(set(c)) == len(c)
     for t in c:
-        assert t & ~0xFF == 0 and t & 3 != 3
+        assert t & ~0x1FF == 0 and t & 3 != 3
         at.describe(t)
     if entry == "queue" and schedule >= L.ME_CIRBP:
         assert {t >> 4 for t in c} == {0, 1, 2, 3} and {t & 3 for t in c} == {1, 2}
