@@ -144,7 +144,7 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
   l.cntS = o; o = align16(o + n_g * 4);
   l.bits = o; o = align16(o + ((N + 31) / 32) * 4);
   l.touched = o; o = align16(o + ((N + 31) / 32) * 4);
-  l.lbase = o; o = align16(o + 33 * 4);
+  l.lbase = o; o = align16(o + ((N + 31) / 32) * 4);
   l.misc = o; o = align16(o + 32 * 4);
   l.total = o;
   return l;
@@ -191,7 +191,7 @@ struct MEState {
   Arr<int32_t> cntS;     // per-group count of the VNs excluded from Algorithm 4's search set
   Arr<uint32_t> bits;    // selection bitmap over VNs
   Arr<uint32_t> touched; // VNs whose D was rewritten in this step
-  Arr<int32_t> lbase;    // compaction: first selection slot of each lane's word range
+  Arr<int32_t> lbase;    // compaction: first selection slot of each bitmap word
   MEMisc* misc;
   const int16_t* tab;
   float fx, ifx;     // FP32 fixed point: 2^k and 2^-k
@@ -289,8 +289,8 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
         // depend on it)
         const int fg = ng - kstar - 1;
         const int members = s.cnt[fg] - s.cntS[fg];
-        if (members > kCap / 2) {
-          const float want = (float)need + 3.0f * sqrtf((float)need) + 8.0f;
+        const float want = (float)need + 3.0f * sqrtf((float)need) + 8.0f;
+        if ((float)members > want) {
           const float t = want / (float)members * 4294967296.0f;
           ms->thr = t >= 4294967040.0f ? 0xffffffffu : (uint32_t)t;
         }
@@ -376,8 +376,9 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
 }
 
 // Compact the selection bitmap into s.sel (ascending), at most np entries; the
-// next step clears the bitmap.  Warp 0 splits the words into 32 ranges and
-// scans their counts; then every warp expands ranges, a lane per bit.
+// next step clears the bitmap.  Warp 0 splits the words into 32 ranges, scans
+// their counts and writes each word's first slot; then every thread expands
+// one word.
 template <int A, class X>
 __device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int np) {
   const int lane = x.tid & 31, warp = x.tid >> 5, nw = x.nt >> 5;
@@ -393,7 +394,11 @@ __device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int
       const int y = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += y;
     }
-    s.lbase[lane] = incl - c;
+    int base = incl - c;
+    for (int w = w0; w < w1; ++w) {
+      s.lbase[w] = base;
+      base += __popc(s.bits[w]);
+    }
     if (lane == 31) s.misc->nsel = min(incl, np);
   }
   x.sync();
@@ -404,15 +409,13 @@ __device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int
     s.misc->ncu = 0;
     s.misc->npp = 0;
   }
-  for (int l = warp; l < 32; l += nw) {
-    int pos = s.lbase[l];
-    if (pos >= np) continue;
-    const int w0 = l * per, w1 = min(words, w0 + per);
-    for (int w = w0; w < w1 && pos < np; ++w) {
-      const uint32_t bw = s.bits[w];
-      const int at = pos + __popc(bw & lanemask_lt());
-      if (((bw >> lane) & 1u) && at < np) s.sel[at] = w * 32 + lane;
-      pos += __popc(bw);
+  for (int w = x.tid; w < words; w += x.nt) {
+    int pos = s.lbase[w];
+    uint32_t bw = s.bits[w];
+    while (bw != 0u && pos < np) {
+      const int bit = __ffs(bw) - 1;
+      bw &= bw - 1u;
+      s.sel[pos++] = w * 32 + bit;
     }
   }
   x.sync();
@@ -751,7 +754,8 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         refresh_vn(j, false);
       }
     }
-    for (int k0 = warp * 32; k0 < nsel; k0 += nt) {
+    // the selected VNs go to the last warps, which have the fewest pair teams
+    for (int k0 = (nw - 1 - warp) * 32; k0 < nsel; k0 += nt) {
       const int k = k0 + lane;
       refresh_vn(k < nsel ? s.sel[k] : -1, false);
     }
@@ -1092,7 +1096,7 @@ bool me_cluster_plan(int arith, const GraphDesc& g, int n_p, int n_g, int cs, in
   // elements and element sizes in array order
   const int64_t n[kClusterArrays] = {g.E, g.E, g.N, g.N, g.N, g.N, g.N, Mw,
                                      n_p, n_p, n_p, n_p, std::max<int64_t>(ncnl, kCap), ncnl, Mw, n_g, n_g,
-                                     Nw, Nw, 33, 1};
+                                     Nw, Nw, Nw, 1};
   const int sz[kClusterArrays] = {msg, msg, llr, llr, dv, 4, 1, 4, 4, 4, 8, 4, 8, 4, 4, 4, 4, 4, 4, 4,
                                   (int)sizeof(MEMisc)};
   ClusterPlan p;
