@@ -766,58 +766,58 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         ms->unsat == 0)
       break;
     if (count >= io.max_updates) break;
-    if (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
+    if constexpr (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
       alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed);  // Alg. 5 line 4
       compact_selection<A, X>(x, N, s, np);
-      continue;
-    }
-    // -- P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of Sec. 5.A:
-    //    N(m*_p)\p), de-duplicated in the selection bitmap
-    for (int k0 = warp * 32; k0 < nsel; k0 += nt) {  // warp-uniform trip count
-      const int k = k0 + lane;
-      bool add = false;
-      int j = 0;
-      if (k < nsel) {
-        const int p = s.sel[k];
-        const unsigned long long rg = s.best[k];
-        const int first = (int)(rg >> 32), npair = (int)(rg & 0xffffffffull);
-        unsigned long long bk = 0ull;
-        for (int i = first; i < first + npair; ++i) {
-          const unsigned long long v = s.cand[i];
-          bk = v > bk ? v : bk;
-        }
-        if (g.vn(p).d == 1) {
-          const typename G::C cc = g.cn(g.ecn(s.est[k]));
-          bk = 0ull;
-          for (int qq = 0; qq < cc.d; ++qq) {
-            const int jj = g.cvn(cc, qq);
-            if (jj == p) continue;
-            const unsigned long long key = ((unsigned long long)mkey(s.D[jj]) << 32) | (0xffffffffu - (uint32_t)jj);
-            bk = key > bk ? key : bk;
+    } else {
+      // -- P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of Sec. 5.A:
+      //    N(m*_p)\p), de-duplicated in the selection bitmap
+      for (int k0 = warp * 32; k0 < nsel; k0 += nt) {  // warp-uniform trip count
+        const int k = k0 + lane;
+        bool add = false;
+        int j = 0;
+        if (k < nsel) {
+          const int p = s.sel[k];
+          const unsigned long long rg = s.best[k];
+          const int first = (int)(rg >> 32), npair = (int)(rg & 0xffffffffull);
+          unsigned long long bk = 0ull;
+          for (int i = first; i < first + npair; ++i) {
+            const unsigned long long v = s.cand[i];
+            bk = v > bk ? v : bk;
+          }
+          if (g.vn(p).d == 1) {
+            const typename G::C cc = g.cn(g.ecn(s.est[k]));
+            bk = 0ull;
+            for (int qq = 0; qq < cc.d; ++qq) {
+              const int jj = g.cvn(cc, qq);
+              if (jj == p) continue;
+              const unsigned long long key = ((unsigned long long)mkey(s.D[jj]) << 32) | (0xffffffffu - (uint32_t)jj);
+              bk = key > bk ? key : bk;
+            }
+          }
+          if (bk != 0ull) {  // else an empty candidate set
+            j = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
+            const uint32_t bit = 1u << (j & 31);
+            add = !(atomicOr(&s.bits[j >> 5], bit) & bit);
           }
         }
-        if (bk != 0ull) {  // else an empty candidate set
-          j = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
-          const uint32_t bit = 1u << (j & 31);
-          add = !(atomicOr(&s.bits[j >> 5], bit) & bit);
+        const unsigned am = __ballot_sync(kFull, add);
+        if (am) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&ms->npp, __popc(am));
+          base = __shfl_sync(kFull, base, 0);
+          if (add) {
+            s.excl[base + __popc(am & lanemask_lt())] = j;
+            const int gj = s.grp[j];
+            agg_add(&s.cntS[gj], gj, 1, am);  // per-group count of P' for Algorithm 4's top-up
+          }
         }
       }
-      const unsigned am = __ballot_sync(kFull, add);
-      if (am) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&ms->npp, __popc(am));
-        base = __shfl_sync(kFull, base, 0);
-        if (add) {
-          s.excl[base + __popc(am & lanemask_lt())] = j;
-          const int gj = s.grp[j];
-          agg_add(&s.cntS[gj], gj, 1, am);  // per-group count of P' for Algorithm 4's top-up
-        }
-      }
+      x.sync();
+      const int npp = ms->npp;
+      if (npp < np) alg4<A, X>(x, s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
+      compact_selection<A, X>(x, N, s, np);
     }
-    x.sync();
-    const int npp = ms->npp;
-    if (npp < np) alg4<A, X>(x, s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
-    compact_selection<A, X>(x, N, s, np);
   }
 
   for (int n = tid; n < N; n += nt) {
