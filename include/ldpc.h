@@ -231,8 +231,9 @@ ldpc_status_t ldpc_encode(const ldpc_code_t *code, const uint8_t *info, int64_t 
  * that holds it and can be resident); else global memory.  A cluster size in
  * tune bits 6-7 selects the cluster form whenever it can run.  The form never
  * changes a result.
- * Errors: INVALID_ARG, UNSUPPORTED (no execution form fits; LDPC_FORM_CLUSTER
- * with a single-edge or flooding schedule), CUDA, NOMEM. */
+ * Errors: INVALID_ARG, UNSUPPORTED (no execution form fits; a check degree
+ * above 32, or a variable degree above 32 for the dynamic schedules;
+ * LDPC_FORM_CLUSTER with a single-edge or flooding schedule), CUDA, NOMEM. */
 ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batch,
                           const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
                           uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);

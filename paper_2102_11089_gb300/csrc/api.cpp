@@ -600,6 +600,7 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
     per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
   } else {
+    if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
     if (p->n_g > 255) return fail(LDPC_ERR_UNSUPPORTED, "n_g > 255 for the multi-edge kernel");
     per = ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g);
     cta_fixed = ldpc::me_smem_per_cta(*g, p->n_p, p->n_g) + 1024;  // + static table headroom

@@ -108,7 +108,7 @@ struct MEBig {
 // Per-CTA working set of one step (always shared memory).  The fill candidates
 // of Algorithm 4 share storage with the affected-check list (not live then).
 struct MESmall {
-  int sel, est, best, excl, cnl, cul, cbits, cnt, cntS, bits, touched, lbase, misc, total;
+  int sel, est, best, cnl, cul, cbits, cnt, cntS, bits, touched, lbase, misc, total;
 };
 
 __host__ __device__ inline MEBig me_big(int arith, int M, int N, int E) {
@@ -136,7 +136,6 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
   l.sel = o; o = align16(o + n_p * 4);
   l.est = o; o = align16(o + n_p * 4);
   l.best = o; o = align16(o + n_p * 8);
-  l.excl = o; o = align16(o + n_p * 4);
   l.cnl = o; o = align16(o + (ncnl > kCap ? ncnl : kCap) * 8);
   l.cul = o; o = align16(o + ncnl * 4);
   l.cbits = o; o = align16(o + ((M + 31) / 32) * 4);
@@ -153,10 +152,8 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
 // shared scalars (misc area)
 struct MEMisc {
   int unsat;
-  int ncn;   // affected (check, owner) pairs this step
-  int ncu;   // distinct affected checks this step
+  int ncnu;  // affected (check, owner) pairs this step | distinct affected checks << 16
   int nsel;  // selected VNs
-  int npp;   // |P'| (ME-LMD)
   int kstar, fill_g, need, top;
   int ncand;
   uint32_t thr, lo, hi;
@@ -182,7 +179,6 @@ struct MEState {
   Arr<int32_t> sel;
   Arr<int32_t> est;
   Arr<unsigned long long> best;
-  Arr<int32_t> excl;   // P' of ME-LMD-CIRBP (excluded from Algorithm 4's top-up)
   Arr<int2> cnl;       // (check, owner k) of every affected check
   Arr<unsigned long long> cand;  // aliases cnl
   Arr<int32_t> cul;    // distinct affected checks
@@ -235,13 +231,6 @@ __device__ __forceinline__ int group_of(float d, int ng) { return min((int)floor
 __device__ __forceinline__ int group_of(uint16_t d, int ng) { return min((int)(((int)d * ng) / 65534), ng - 1); }
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
-
-// *at += v from the lanes of `mask` (the calling lanes; all of them must
-// call; at = &counter[idx]), one atomic per distinct idx.
-__device__ __forceinline__ void agg_add(int32_t* at, int idx, int v, unsigned mask) {
-  const unsigned peers = __match_any_sync(mask, idx);
-  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(at, v * __popc(peers));
-}
 
 // Algorithm 4 over S = O_N minus nexcl excluded VNs (their bits are set and
 // s.cntS counts them per group): sets the bits of the selected VNs (at most
@@ -313,16 +302,17 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
       const int q = q0 + lane;
       unsigned fm = 0;
       if (q < nq) {
+        // the quad's four group bytes compared at once (per-byte SIMD compares,
+        // then the byte masks packed to nibbles); VNs past N or already in
+        // the bitmap are not live; Q(k*) members go in with one atomic
         const uint32_t g4 = *(const uint32_t*)&s.grp[4 * q];
-        const unsigned ex = (s.bits[q >> 3] >> ((q & 7) * 4)) & 0xfu;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int n = 4 * q + i;
-          if (n >= N || ((ex >> i) & 1u)) continue;
-          const int gi = (int)((g4 >> (8 * i)) & 0xffu);
-          if (iter == 0 && gi >= top) atomicOr(&s.bits[n >> 5], 1u << (n & 31));
-          if (gi == fg) fm |= 1u << i;
-        }
+        const int sh = (q & 7) * 4;
+        const unsigned live = (N - 4 * q >= 4 ? 0xfu : ((1u << (N - 4 * q)) - 1u)) & ~((s.bits[q >> 3] >> sh) & 0xfu);
+        const uint32_t ge = __vcmpgeu4(g4, (uint32_t)top * 0x01010101u);
+        const uint32_t eq = __vcmpeq4(g4, (uint32_t)(fg & 0xff) * 0x01010101u);  // fg = -1: byte 255, no group
+        const unsigned gem = ((((ge >> 7) & 0x01010101u) * 0x01020408u) >> 24) & live;
+        fm = ((((eq >> 7) & 0x01010101u) * 0x01020408u) >> 24) & live;
+        if (iter == 0 && gem) atomicOr(&s.bits[q >> 3], gem << sh);
       }
       if (!fill) continue;
       uint32_t w[4] = {(uint32_t)q, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
@@ -402,13 +392,6 @@ __device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int
     if (lane == 31) s.misc->nsel = min(incl, np);
   }
   x.sync();
-  // the step counters are reset only here: until the barrier above some
-  // thread may still be reading npp (whether to run Algorithm 4)
-  if (x.tid == 0) {
-    s.misc->ncn = 0;
-    s.misc->ncu = 0;
-    s.misc->npp = 0;
-  }
   for (int w = x.tid; w < words; w += x.nt) {
     int pos = s.lbase[w];
     uint32_t bw = s.bits[w];
@@ -443,7 +426,6 @@ __device__ __forceinline__ MEState<A, CtaX> cta_state(const GraphDesc& gd, const
   s.sel.p = (int32_t*)(small + ls.sel);
   s.est.p = (int32_t*)(small + ls.est);
   s.best.p = (unsigned long long*)(small + ls.best);
-  s.excl.p = (int32_t*)(small + ls.excl);
   s.cnl.p = (int2*)(small + ls.cnl);
   s.cul.p = (int32_t*)(small + ls.cul);
   s.cand.p = (unsigned long long*)(small + ls.cnl);
@@ -508,9 +490,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
   }
   if (tid == 0) {
     ms->unsat = 0;
-    ms->ncn = 0;
-    ms->ncu = 0;
-    ms->npp = 0;
+    ms->ncnu = 0;
   }
   if (x.sync_or(bad, &ms->orflag)) {
     for (int n = tid; n < N; n += nt) {
@@ -557,8 +537,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
       s.D[n] = d;
       s.grp[n] = (uint8_t)gi;
     }
-    const unsigned am = __ballot_sync(kFull, act);
-    if (act) agg_add(&s.cnt[gi], gi, 1, am);
+    if (act) atomicAdd(&s.cnt[gi], 1);
   }
   x.sync();
 
@@ -591,10 +570,9 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         }
       }
     }
-    const unsigned cm = __ballot_sync(kFull, ch);
-    if (ch) {
-      agg_add(&s.cnt[go], go, -1, cm);
-      agg_add(&s.cnt[gn], gn, 1, cm);
+    if (ch) {  // per-lane atomics: aggregating equal groups first (match) costs more
+      atomicAdd(&s.cnt[go], -1);
+      atomicAdd(&s.cnt[gn], 1);
     }
     return d;
   };
@@ -680,28 +658,23 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         const uint32_t bit = 1u << (m & 31);
         first = !(atomicOr(&s.cbits[m >> 5], bit) & bit);
       }
-      const unsigned bal = __ballot_sync(kFull, aff);
-      int base = 0;
-      if (bal) {
-        if (lane == 0) base = atomicAdd(&ms->ncn, __popc(bal));
-        base = __shfl_sync(kFull, base, 0);
-        if (aff) s.cnl[base + __popc(bal & lanemask_lt())] = make_int2(m, k);
-      }
+      // list slots of the warp's pairs and new checks from one atomic on the
+      // packed counts (pairs in the low half, checks in the high half)
+      const unsigned bal = __ballot_sync(kFull, aff), bf = __ballot_sync(kFull, first);
+      int bases = 0;
+      if (lane == 0 && (bal | bf) != 0u) bases = atomicAdd(&ms->ncnu, __popc(bal) | (__popc(bf) << 16));
+      bases = __shfl_sync(kFull, bases, 0);
+      const int base = bases & 0xffff;
+      if (aff) s.cnl[base + __popc(bal & lanemask_lt())] = make_int2(m, k);
+      if (first) s.cul[(bases >> 16) + __popc(bf & lanemask_lt())] = m;
       if (act && q == 0) {  // p's pairs are one block of the list: (first << 32) | count
         const unsigned tm = (Wv == 32 ? kFull : ((1u << Wv) - 1u)) << (vteam * Wv);
         const unsigned below = (1u << (vteam * Wv)) - 1u;
         s.best[k] = ((unsigned long long)(unsigned)(base + __popc(bal & below)) << 32) | (unsigned)__popc(bal & tm);
       }
-      const unsigned bf = __ballot_sync(kFull, first);
-      if (bf) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&ms->ncu, __popc(bf));
-        base = __shfl_sync(kFull, base, 0);
-        if (first) s.cul[base + __popc(bf & lanemask_lt())] = m;
-      }
     }
     x.sync();
-    const int ncn = ms->ncn, ncu = ms->ncu;
+    const int ncn = ms->ncnu & 0xffff, ncu = ms->ncnu >> 16;
     // -- precomputed C2V of every affected check (once per check); the L~ sums
     //    of its variables follow by exact deltas
     for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
@@ -760,6 +733,9 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
       refresh_vn(k < nsel ? s.sel[k] : -1, false);
     }
     x.sync();
+    // the pair and check counts were read after the commit barrier; the next
+    // commit phase, which counts again, starts after at least one more barrier
+    if (tid == 0) ms->ncnu = 0;
     count += nsel;
     ++step;
     if (a.check_interval > 0 && (count / a.check_interval) > ((count - nsel) / a.check_interval) &&
@@ -801,20 +777,13 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
             add = !(atomicOr(&s.bits[j >> 5], bit) & bit);
           }
         }
-        const unsigned am = __ballot_sync(kFull, add);
-        if (am) {
-          int base = 0;
-          if (lane == 0) base = atomicAdd(&ms->npp, __popc(am));
-          base = __shfl_sync(kFull, base, 0);
-          if (add) {
-            s.excl[base + __popc(am & lanemask_lt())] = j;
-            const int gj = s.grp[j];
-            agg_add(&s.cntS[gj], gj, 1, am);  // per-group count of P' for Algorithm 4's top-up
-          }
-        }
+        if (add) atomicAdd(&s.cntS[s.grp[j]], 1);  // per-group count of P' for Algorithm 4's top-up
       }
       x.sync();
-      const int npp = ms->npp;
+      // |P'| = the sum of its per-group counts (every warp, same value)
+      int npp = 0;
+      for (int i = lane; i < ng; i += 32) npp += s.cntS[i];
+      npp = __reduce_add_sync(kFull, npp);
       if (npp < np) alg4<A, X>(x, s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
       compact_selection<A, X>(x, N, s, np);
     }
@@ -947,18 +916,17 @@ __device__ __forceinline__ MEState<A, ClusterX> cluster_state(const DecodeArgs& 
   LDPC_DARR(sel, int32_t, 8);
   LDPC_DARR(est, int32_t, 9);
   LDPC_DARR(best, unsigned long long, 10);
-  LDPC_DARR(excl, int32_t, 11);
-  LDPC_DARR(cnl, int2, 12);
-  LDPC_DARR(cand, unsigned long long, 12);
-  LDPC_DARR(cul, int32_t, 13);
-  LDPC_DARR(cbits, uint32_t, 14);
-  LDPC_DARR(cnt, int32_t, 15);
-  LDPC_DARR(cntS, int32_t, 16);
-  LDPC_DARR(bits, uint32_t, 17);
-  LDPC_DARR(touched, uint32_t, 18);
-  LDPC_DARR(lbase, int32_t, 19);
+  LDPC_DARR(cnl, int2, 11);
+  LDPC_DARR(cand, unsigned long long, 11);
+  LDPC_DARR(cul, int32_t, 12);
+  LDPC_DARR(cbits, uint32_t, 13);
+  LDPC_DARR(cnt, int32_t, 14);
+  LDPC_DARR(cntS, int32_t, 15);
+  LDPC_DARR(bits, uint32_t, 16);
+  LDPC_DARR(touched, uint32_t, 17);
+  LDPC_DARR(lbase, int32_t, 18);
 #undef LDPC_DARR
-  s.misc = cg::this_cluster().map_shared_rank((MEMisc*)(base + c.off[20]), (unsigned)c.rank0[20]);
+  s.misc = cg::this_cluster().map_shared_rank((MEMisc*)(base + c.off[19]), (unsigned)c.rank0[19]);
   s.tab = tab_int;
   return s;
 }
@@ -974,8 +942,8 @@ __global__ void __launch_bounds__(TPB, 1) me_cluster_kernel(const DecodeArgs a) 
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   const cg::cluster_group cl = cg::this_cluster();
   unsigned char* base = smem_raw + a.graph_smem;
-  if (cl.block_rank() == (unsigned)a.cl.rank0[20] && threadIdx.x == 0)
-    ((MEMisc*)(base + a.cl.off[20]))->orflag = 0;
+  if (cl.block_rank() == (unsigned)a.cl.rank0[19] && threadIdx.x == 0)
+    ((MEMisc*)(base + a.cl.off[19]))->orflag = 0;
   const ClusterX x;
   x.sync();  // every CTA of the cluster runs before any distributed address is formed
   MEState<A, ClusterX> s = cluster_state<A>(a, base, tab_int);
@@ -1095,9 +1063,9 @@ bool me_cluster_plan(int arith, const GraphDesc& g, int n_p, int n_g, int cs, in
   const int64_t Mw = (g.M + 31) / 32, Nw = (g.N + 31) / 32;
   // elements and element sizes in array order
   const int64_t n[kClusterArrays] = {g.E, g.E, g.N, g.N, g.N, g.N, g.N, Mw,
-                                     n_p, n_p, n_p, n_p, std::max<int64_t>(ncnl, kCap), ncnl, Mw, n_g, n_g,
+                                     n_p, n_p, n_p, std::max<int64_t>(ncnl, kCap), ncnl, Mw, n_g, n_g,
                                      Nw, Nw, Nw, 1};
-  const int sz[kClusterArrays] = {msg, msg, llr, llr, dv, 4, 1, 4, 4, 4, 8, 4, 8, 4, 4, 4, 4, 4, 4, 4,
+  const int sz[kClusterArrays] = {msg, msg, llr, llr, dv, 4, 1, 4, 4, 4, 8, 8, 4, 4, 4, 4, 4, 4, 4,
                                   (int)sizeof(MEMisc)};
   ClusterPlan p;
   std::memset(&p, 0, sizeof(p));

@@ -87,8 +87,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
   if (v.dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
-  if (ldpc::is_single_edge(p->schedule) && v.dv_max > 32)
-    return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
+  if (p->schedule != LDPC_FLOODING && v.dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

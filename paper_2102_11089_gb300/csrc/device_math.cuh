@@ -35,20 +35,21 @@ __device__ __forceinline__ float one_minus_exp_small(float x) {
 // (truncation < 5e-9 relative); above, ln((1+t)/(1-t)) with 1 - t from the Taylor
 // polynomial when x < 1/4 (no cancellation) and MUFU lg2.  Relative error ~1e-6
 // (the exponential itself is the accurate expf: MUFU ex2 alone loses |x| 1e-7).
+// Both forms are evaluated and one selected: the lanes of a check team take
+// both sides, and a branch would run them one after the other.
 __device__ __forceinline__ float phi_f(float x) {
   const float t = expf(-x);
-  if (t <= 0.25f) {
-    const float t2 = t * t;
-    float p = 1.0f / 11.0f;
-    p = fmaf(p, t2, 1.0f / 9.0f);
-    p = fmaf(p, t2, 1.0f / 7.0f);
-    p = fmaf(p, t2, 0.2f);
-    p = fmaf(p, t2, 1.0f / 3.0f);
-    p = fmaf(p, t2, 1.0f);
-    return 2.0f * t * p;
-  }
+  const float t2 = t * t;
+  float p = 1.0f / 11.0f;
+  p = fmaf(p, t2, 1.0f / 9.0f);
+  p = fmaf(p, t2, 1.0f / 7.0f);
+  p = fmaf(p, t2, 0.2f);
+  p = fmaf(p, t2, 1.0f / 3.0f);
+  p = fmaf(p, t2, 1.0f);
+  const float series = 2.0f * t * p;
   const float omt = x < 0.25f ? one_minus_exp_small(x) : 1.0f - t;
-  return __logf(__fdividef(1.0f + t, omt));
+  const float lg = __logf(__fdividef(1.0f + t, omt));
+  return t <= 0.25f ? series : lg;
 }
 
 // The encoded V2C input of a check: phi(|V| clipped) with the sign of V in the
@@ -70,14 +71,15 @@ __device__ __forceinline__ int8_t encode_int(int v) { return (int8_t)max(-31, mi
 // 1 - 1: with x = |a|, y = |b|, ex = e^-x, ey = e^-y,
 //   equal signs    : e^-min(x,y) (1 - e^-|x-y|) / ((1+ex)(1+ey))
 //   opposite signs : ((1-ex)/(1+ex) + (1-ey)/(1+ey)) / 2  (= (tanh(x/2)+tanh(y/2))/2)
+// Both are evaluated and one selected (no divergent branch in a lane team).
 __device__ __forceinline__ float ci_fp(float a, float b) {
   const float x = fabsf(a), y = fabsf(b);
   const float ex = expf(-x), ey = expf(-y);
-  if ((a >= 0.0f) != (b >= 0.0f))
-    return 0.5f * (__fdividef(1.0f - ex, 1.0f + ex) + __fdividef(1.0f - ey, 1.0f + ey));
+  const float opposite = 0.5f * (__fdividef(1.0f - ex, 1.0f + ex) + __fdividef(1.0f - ey, 1.0f + ey));
   const float d = fabsf(x - y);
   const float omd = d < 0.25f ? one_minus_exp_small(d) : 1.0f - expf(-d);
-  return __fdividef(fmaxf(ex, ey) * omd, (1.0f + ex) * (1.0f + ey));
+  const float equal = __fdividef(fmaxf(ex, ey) * omd, (1.0f + ex) * (1.0f + ey));
+  return (a >= 0.0f) != (b >= 0.0f) ? opposite : equal;
 }
 
 // Integer CI: |T[c(a)] - T[c(b)]| with c = clamp to [-127, 127].
@@ -140,7 +142,9 @@ __device__ __forceinline__ int team_c2v(const G& g, const CA& C, const LA& L, in
   // lane r takes prefix(r - 1) (+) suffix(r + 1); the sign is the team parity
   // with r's own sign removed
   if (A == kFP32) {
-    const float enc = r < dc ? encode_fp((float)L[j] - (float)C[e], clip) : 0.0f;
+    // idle lanes (e = j = 0) compute too and drop the value: no branch around phi
+    const float enc0 = encode_fp((float)L[j] - (float)C[e], clip);
+    const float enc = r < dc ? enc0 : 0.0f;
     const unsigned sg = __float_as_uint(enc) >> 31;
     unsigned sall = sg;
     float pre = fabsf(enc), suf = pre;

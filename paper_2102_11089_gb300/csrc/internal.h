@@ -46,7 +46,7 @@ struct GraphDesc {
 // in the shared memory of the CTAs of a cluster.  Element i of array k is in
 // rank rank0[k] + (i >> shift[k]), at byte off[k] + (i & (2^shift[k] - 1)) *
 // element size from the start of that CTA's state area.
-constexpr int kClusterArrays = 21;  // C P lam L D Lt grp par | sel est best excl cnl cul cbits cnt cntS bits touched lbase misc
+constexpr int kClusterArrays = 20;  // C P lam L D Lt grp par | sel est best cnl cul cbits cnt cntS bits touched lbase misc
 struct ClusterPlan {
   int32_t cs;     // CTAs per cluster (0: not the cluster form)
   int32_t bytes;  // state bytes per CTA
