@@ -541,6 +541,9 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
     return fail(LDPC_ERR_UNSUPPORTED, "the cluster form runs the multi-edge schedules");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
+  // lane teams: a check (every schedule) or a variable (dynamic schedules) within one warp
+  if (code->dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
+  if (p->schedule != LDPC_FLOODING && code->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
 
   const ldpc::GraphDesc* g;
   ldpc_status_t st = ensure_device(const_cast<ldpc_code_t*>(code), &g, nullptr);
@@ -586,7 +589,6 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   const int optin = max_optin_smem();
   const cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e;
-  if (g->dc_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "check degree > 32");
   const int gsm = a.graph_smem;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -597,10 +599,8 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   if (p->schedule == LDPC_FLOODING) {
     per = ldpc::flood_smem_per_frame(arith, *g);
   } else if (ldpc::is_single_edge(p->schedule)) {
-    if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
     per = ldpc::se_smem_per_frame(arith, p->schedule, *g);
   } else {
-    if (g->dv_max > 32) return fail(LDPC_ERR_UNSUPPORTED, "variable degree > 32");
     if (p->n_g > 255) return fail(LDPC_ERR_UNSUPPORTED, "n_g > 255 for the multi-edge kernel");
     per = ldpc::me_smem_per_frame(arith, p->schedule, *g, p->n_p, p->n_g);
     cta_fixed = ldpc::me_smem_per_cta(*g, p->n_p, p->n_g) + 1024;  // + static table headroom

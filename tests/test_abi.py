@@ -156,6 +156,27 @@ def test_decode_validation_needs_no_gpu(lib):
     assert lib.ldpc_awgn_llr(code._h, null, 3, 0, 0, null, null, ctypes.c_float(0.5), null) == -1
 
 
+def test_decode_degree_limits_need_no_gpu(lib):
+    """Lane teams hold a check (every schedule) or a variable (dynamic schedules)
+    within one warp: degrees above 32 are refused before any device work."""
+    null = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    # variable 0 in 33 checks (plus a second edge per check so no check is degree 1)
+    chk = [m for m in range(33) for _ in range(2)]
+    var = [v for m in range(33) for v in (0, 1 + m)]
+    wide_v = L.Code.from_edges(np.array(chk, np.int32), np.array(var, np.int32), 33, 34, 1)
+    # check 0 on 33 variables
+    chk2 = [0] * 33 + list(range(1, 34))
+    var2 = list(range(33)) + list(range(33))
+    wide_c = L.Code.from_edges(np.array(chk2, np.int32), np.array(var2, np.int32), 34, 33, 1)
+    for sched in ("me-cirbp", "me-lmd-cirbp", "lmd-cirbp", "cirbp", "rbp", "lmdrbp"):
+        q = L.make_params(sched, max_updates=10)
+        assert lib.ldpc_decode(wide_v._h, dummy, 4, ctypes.byref(q), null, null, null, null, null, null) == -5, sched
+    for sched in ("flooding", "me-lmd-cirbp", "lmd-cirbp"):
+        q = L.make_params(sched, max_updates=10)
+        assert lib.ldpc_decode(wide_c._h, dummy, 4, ctypes.byref(q), null, null, null, null, null, null) == -5, sched
+
+
 def test_default_params(lib):
     p = L.DecodeParams()
     assert lib.ldpc_default_params(ctypes.byref(p)) == 0
