@@ -179,10 +179,10 @@ def profiled_traffic(args, batch):
     text = open(path).read()
     m = re.search(r"digest \(decode_me.cu,\s+device_math.cuh, graph.cuh\): ([0-9a-f]{12})", text)
     t = re.search(r"DRAM traffic per full bench launch \(65,536 frames, scaled by frames\): ([0-9.]+) MB", text)
-    w = re.search(r"shared wavefronts \| ([0-9.]+) G", text)
+    i = re.search(r"\| issue active \| ([0-9.]+) % \|", text)
     if not m or not t or m.group(1) != kernel_digest():
         return None, None
-    return float(t.group(1)) * 1e6 * batch / 65536, (float(w.group(1)) if w else None)
+    return float(t.group(1)) * 1e6 * batch / 65536, (float(i.group(1)) if i else None)
 
 
 def measured_peaks():
@@ -403,7 +403,7 @@ def run_ours(args):
     sm_count = props.multi_processor_count
     clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     smem_peak = sm_count * SMEM_BYTES_PER_CLK_PER_SM * clk_mhz * 1e6 / 1e9
-    traffic, wavefronts_g = profiled_traffic(args, B)
+    traffic, issue_pct = profiled_traffic(args, B)
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
                 "frac": achieved / smem_peak, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch (ncu, 16,384-frame capture scaled by frames); "
@@ -412,7 +412,10 @@ def run_ours(args):
                                f"{clk_mhz:.0f} MHz (shared memory is not in MEASURED_PEAKS)",
                 "kernel": f"me_decode_kernel ({args.schedule}, {args.arith})",
                 "bytes_per_update": bpu, "updates_per_launch": upd_total / args.steps,
-                "launch_ms": dec_avg, "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks": peaks_kind}
+                "launch_ms": dec_avg, "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks": peaks_kind,
+                "issue_active_pct": issue_pct,
+                "binder": "instruction issue and the barriers between the phases of a step (ncu issue-active "
+                          "share of the same kernel source, profiles/me_decode_kernel_wifi_n2304_fp32.md)"}
 
     # ---- end to end through host buffers: H2D Eb/N0 values, D2H decisions + counters
     eb_host = torch.full((B,), args.ebn0, dtype=torch.float32).pin_memory()
