@@ -53,6 +53,20 @@ def test_int6_bitexact_check_intervals_and_ragged_budgets(schedule, ci, budget):
     assert_bitexact(g, o, schedule)
 
 
+@pytest.mark.parametrize("schedule", ALL)
+@pytest.mark.parametrize("N,dv,dc", [(102, 3, 6), (99, 3, 9)])
+def test_int6_bitexact_n_not_a_multiple_of_four(schedule, N, dv, dc):
+    # the last VN quad of Algorithm 4's pass (and the last bitmap word) is partial
+    c, v, m = wl.regular_code(N, dv, dc, 3)
+    spec = (c, v, m, N, N - m, None)
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 200, 1.75, 515), 0.5)
+    kw = dict(schedule=schedule, max_updates=10 * code.E, gamma=0.1, n_p=7, n_g=6, seed=11)
+    g = run_gpu(code, q, torch, arith="int6", **kw)
+    o = run_oracle(spec, q, "int6", **kw)
+    assert_bitexact(g, o, schedule)
+
+
 @pytest.mark.parametrize("schedule,n_p", [("flooding", 0), ("rbp", 0), ("cirbp", 0),
                                           ("lmd-cirbp", 0), ("me-cirbp", 64),
                                           ("me-lmd-cirbp", 4), ("me-lmd-cirbp", 16),
