@@ -175,6 +175,11 @@ def test_decode_degree_limits_need_no_gpu(lib):
     for sched in ("flooding", "me-lmd-cirbp", "lmd-cirbp"):
         q = L.make_params(sched, max_updates=10)
         assert lib.ldpc_decode(wide_c._h, dummy, 4, ctypes.byref(q), null, null, null, null, null, null) == -5, sched
+    # the no-allocation entry point applies the same limits
+    for code, sched in ((wide_v, "me-lmd-cirbp"), (wide_v, "lmd-cirbp"), (wide_c, "flooding")):
+        q = L.make_params(sched, max_updates=10)
+        assert lib.ldpc_decode_noalloc(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
+                                       null) == -5, sched
 
 
 def test_default_params(lib):
