@@ -67,6 +67,23 @@ def test_int6_bitexact_n_not_a_multiple_of_four(schedule, N, dv, dc):
     assert_bitexact(g, o, schedule)
 
 
+@pytest.mark.parametrize("schedule", ["me-cirbp", "me-lmd-cirbp"])
+@pytest.mark.parametrize("n_g", [200, 255])
+def test_int6_bitexact_many_groups(schedule, n_g):
+    # group indices past a nibble: Algorithm 4's per-byte group tests up to N_G - 1 = 254
+    spec = regular96()
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 200, 1.5, 4242), 0.5)
+    kw = dict(schedule=schedule, max_updates=10 * code.E, gamma=0.1, n_p=6, n_g=n_g, seed=13)
+    g = run_gpu(code, q, torch, arith="int6", **kw)
+    o = run_oracle(spec, q, "int6", **kw)
+    assert_bitexact(g, o, schedule)
+    lam = llrs(spec, 100, 1.5, 4243)
+    g = run_gpu(code, lam, torch, arith="fp32", **kw)
+    o = run_oracle(spec, lam, "fp32", **kw)
+    trace_prefix_ok(g, o)
+
+
 @pytest.mark.parametrize("schedule,n_p", [("flooding", 0), ("rbp", 0), ("cirbp", 0),
                                           ("lmd-cirbp", 0), ("me-cirbp", 64),
                                           ("me-lmd-cirbp", 4), ("me-lmd-cirbp", 16),
