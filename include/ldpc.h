@@ -238,6 +238,35 @@ ldpc_status_t ldpc_decode(const ldpc_code_t *code, const void *llr, int64_t batc
                           const ldpc_decode_params_t *params, uint8_t *hard, int64_t *updates,
                           uint8_t *converged, int32_t *trace, float *llr_out, void *cuda_stream);
 
+/* Outputs of ldpc_decode_ex: every pointer is a device pointer or NULL.  The
+ * first five are those of ldpc_decode; the others expose the decoder's final
+ * message state and its fallback count, for checks against a reference
+ * decoder and for the statistics of Sec. 3.A / Sec. 5.A.
+ * c2v_out   : float[batch][n_edges]: final committed C2V messages L^C (the terms
+ *             of eq. 3), edge ids as in ldpc_code_edges (INT6: integer values)
+ * pre_out   : float[batch][n_edges]: final precomputed C2V messages L~^C of
+ *             eq. (2) (dynamic schedules only; flooding keeps none)
+ * fallbacks : int64[batch]: CIRBP updates whose edge came from the residual
+ *             fallback of Alg. 1 line 6 (D_{n*} < gamma); 0 for the other
+ *             schedules.  fallbacks / updates is the kappa of Sec. 5.A. */
+typedef struct {
+    uint8_t *hard;
+    int64_t *updates;
+    uint8_t *converged;
+    int32_t *trace;
+    float *llr_out;
+    float *c2v_out;
+    float *pre_out;
+    int64_t *fallbacks;
+} ldpc_decode_outputs_t;
+
+/* ldpc_decode with the extended outputs above (out may not be NULL).  Same
+ * arguments, forms and errors as ldpc_decode; pre_out with LDPC_FLOODING is
+ * INVALID_ARG. */
+ldpc_status_t ldpc_decode_ex(const ldpc_code_t *code, const void *llr, int64_t batch,
+                             const ldpc_decode_params_t *params, const ldpc_decode_outputs_t *out,
+                             void *cuda_stream);
+
 /* Decode a work queue of frames from up to 16 codes lifted from protographs
  * (ldpc_code_build_qc), each frame with its own budget; the persistent form of
  * the batched decoder.  In LDPC_QUEUE_PERSISTENT mode one launch of resident
@@ -272,9 +301,11 @@ ldpc_status_t ldpc_decode_queue(const ldpc_code_t *const *codes, int32_t n_codes
  * no counterpart: this is a service of the library, not a step of the method.
  *
  * Who needs it: callers that must not allocate at the moment they decode --
- * for example code that runs while its stream is being captured into a CUDA
- * graph, real-time loops that must not enter the allocator, or processes with
- * a memory budget fixed at start-up.  ldpc_decode allocates the per-frame
+ * real-time loops that must not enter the CUDA allocator (it can block on the
+ * device or on locks for an unbounded time), processes whose device memory is
+ * handed out up front to another allocator or capped by a fixed budget, and
+ * plug-ins running inside a host application that owns every allocation.
+ * ldpc_decode allocates the per-frame
  * state slots of its global-memory form and uploads a code on its first use
  * on a device; this entry point calls no cudaMalloc, cudaFree or other
  * allocating routine.  Instead it always uses the global-memory form on one

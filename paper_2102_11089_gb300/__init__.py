@@ -55,6 +55,11 @@ class DecodeParams(ctypes.Structure):
     ]
 
 
+class DecodeOutputs(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in
+                ("hard", "updates", "converged", "trace", "llr_out", "c2v_out", "pre_out", "fallbacks")]
+
+
 class CodeInfo(ctypes.Structure):
     _fields_ = [
         ("n_checks", ctypes.c_int32), ("n_vars", ctypes.c_int32), ("n_edges", ctypes.c_int64),
@@ -87,6 +92,7 @@ def _load():
             ("ldpc_awgn_llr", [P, P, I64, U64, U64, P, P, ctypes.c_float, P]),
             ("ldpc_decode", [P, P, I64, P, P, P, P, P, P, P]),
             ("ldpc_decode_noalloc", [P, P, I64, P, P, P, P, P, P, P]),
+            ("ldpc_decode_ex", [P, P, I64, P, P, P]),
             ("ldpc_decode_queue", [P, I32, P, I64, P, P, P, P, P, I32, P]),
             ("ldpc_wbp_forward", [P, P, I64, P, P, I64, P, ctypes.c_float, P, P, P, P]),
             ("ldpc_ci_stats", [P, P, I64, I32, P, P]),
@@ -196,10 +202,12 @@ def make_params(schedule="lmd-cirbp", arith="fp32", *, gamma=0.1, n_p=16, n_g=16
 
 
 def decode(code: Code, llr, params: DecodeParams | None = None, *, want_trace=False,
-           want_llr=False, stream=None, out=None, **kw):
+           want_llr=False, want_msgs=False, want_fallbacks=False, stream=None, out=None, **kw):
     """Decode a [batch, N] device tensor of channel LLRs (float32, or int8 for
     INT6).  Returns a dict of device tensors: hard, updates, converged and
-    optionally trace / llr."""
+    optionally trace / llr; with want_msgs the final messages c2v [batch, E]
+    (L^C) and, for the dynamic schedules, pre [batch, E] (L~^C); with
+    want_fallbacks the CIRBP fallback counts [batch] (ldpc_decode_ex)."""
     import torch
     if params is None:
         params = make_params(**kw)
@@ -219,11 +227,24 @@ def decode(code: Code, llr, params: DecodeParams | None = None, *, want_trace=Fa
                                       device=dev)
         if want_llr:
             out["llr"] = torch.empty((B, code.N), dtype=torch.float32, device=dev)
+        if want_msgs:
+            out["c2v"] = torch.empty((B, code.E), dtype=torch.float32, device=dev)
+            if params.schedule != FLOODING:
+                out["pre"] = torch.empty((B, code.E), dtype=torch.float32, device=dev)
+        if want_fallbacks:
+            out["fallbacks"] = torch.empty(B, dtype=torch.int64, device=dev)
 
     def ptr(name):
         t = out.get(name)
         return None if t is None else ctypes.c_void_p(t.data_ptr())
 
+    if any(k in out for k in ("c2v", "pre", "fallbacks")):
+        o = DecodeOutputs(*[None if t is None else t.value for t in
+                            (ptr("hard"), ptr("updates"), ptr("converged"), ptr("trace"), ptr("llr"),
+                             ptr("c2v"), ptr("pre"), ptr("fallbacks"))])
+        _check(_load().ldpc_decode_ex(code._h, ctypes.c_void_p(llr.data_ptr()), B, ctypes.byref(params),
+                                      ctypes.byref(o), _stream_ptr(stream)))
+        return out
     _check(_load().ldpc_decode(code._h, ctypes.c_void_p(llr.data_ptr()), B, ctypes.byref(params),
                                ptr("hard"), ptr("updates"), ptr("converged"), ptr("trace"),
                                ptr("llr"), _stream_ptr(stream)))

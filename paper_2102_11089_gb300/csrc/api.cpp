@@ -522,7 +522,20 @@ ldpc_status_t ldpc_encode(const ldpc_code_t* code, const uint8_t* info, int64_t 
 ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batch,
                           const ldpc_decode_params_t* p, uint8_t* hard, int64_t* updates, uint8_t* converged,
                           int32_t* trace, float* llr_out, void* cuda_stream) {
-  if (!code || !p) return fail(LDPC_ERR_INVALID_ARG, "code and params are required");
+  ldpc_decode_outputs_t o;
+  std::memset(&o, 0, sizeof(o));
+  o.hard = hard;
+  o.updates = updates;
+  o.converged = converged;
+  o.trace = trace;
+  o.llr_out = llr_out;
+  return ldpc_decode_ex(code, llr, batch, p, &o, cuda_stream);
+}
+
+ldpc_status_t ldpc_decode_ex(const ldpc_code_t* code, const void* llr, int64_t batch,
+                             const ldpc_decode_params_t* p, const ldpc_decode_outputs_t* o, void* cuda_stream) {
+  if (!code || !p || !o) return fail(LDPC_ERR_INVALID_ARG, "code, params and outputs are required");
+  if (o->pre_out && p->schedule == LDPC_FLOODING) return fail(LDPC_ERR_INVALID_ARG, "flooding keeps no L~^C");
   if (batch < 0) return fail(LDPC_ERR_INVALID_ARG, "batch < 0");
   if (p->schedule < LDPC_FLOODING || p->schedule > LDPC_SLMDRBP)
     return fail(LDPC_ERR_INVALID_ARG, "unknown schedule");
@@ -559,11 +572,14 @@ ldpc_status_t ldpc_decode(const ldpc_code_t* code, const void* llr, int64_t batc
   a.g = *g;
   a.llr = llr;
   a.batch = batch;
-  a.hard = hard;
-  a.updates = updates;
-  a.converged = converged;
-  a.trace = trace;
-  a.llr_out = llr_out;
+  a.hard = o->hard;
+  a.updates = o->updates;
+  a.converged = o->converged;
+  a.trace = o->trace;
+  a.llr_out = o->llr_out;
+  a.c2v_out = o->c2v_out;
+  a.pre_out = o->pre_out;
+  a.fallbacks = o->fallbacks;
   a.max_updates = p->max_updates;
   a.check_interval = p->check_interval;
   a.gamma_f = (float)p->gamma;

@@ -88,9 +88,12 @@ __device__ __forceinline__ void flood_frame(const DecodeArgs& a, const G& g, int
     if (a.hard) a.hard[b * N + n] = (uint8_t)(L[n] < (L_)0);
     if (a.llr_out) a.llr_out[b * N + n] = (float)L[n];
   }
+  if (a.c2v_out)
+    for (int e = tid; e < E; e += nt) a.c2v_out[b * (int64_t)E + e] = (float)C[e];
   if (tid == 0) {
     if (a.updates) a.updates[b] = count;
     if (a.converged) a.converged[b] = (uint8_t)conv;
+    if (a.fallbacks) a.fallbacks[b] = 0;
   }
   __syncthreads();
 }

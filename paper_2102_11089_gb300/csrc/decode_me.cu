@@ -793,9 +793,14 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     if (io.hard) io.hard[n] = (uint8_t)(s.L[n] < (L_)0);
     if (io.llr_out) io.llr_out[n] = (float)s.L[n];
   }
+  for (int e = tid; e < E; e += nt) {
+    if (io.c2v_out) io.c2v_out[e] = (float)s.C[e];
+    if (io.pre_out) io.pre_out[e] = (float)s.P[e];
+  }
   if (tid == 0) {
     if (io.updates) *io.updates = count;
     if (io.converged) *io.converged = ms->unsat == 0 ? 1 : 0;
+    if (io.fallbacks) *io.fallbacks = 0;
   }
   x.sync();
 }
@@ -878,7 +883,7 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_queue_ke
       cur = it.code;
     }
     const int elem = A == kINT6 ? 1 : 4;
-    FrameIO io;
+    FrameIO io = empty_io();
     io.llr = (const unsigned char*)q.a.llr + it.llr_offset * elem;
     io.hard = q.a.hard ? q.a.hard + it.out_offset : nullptr;
     io.llr_out = nullptr;

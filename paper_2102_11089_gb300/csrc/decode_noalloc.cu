@@ -1,12 +1,14 @@
 // decode_noalloc.cu -- ldpc_decode_noalloc: decoding that allocates no memory.
 //
-// Some callers cannot allocate device memory at the moment they decode: code
-// running while a CUDA stream is being captured into a graph (an allocation
-// there is either refused or recorded into the graph), real-time loops that
-// must not touch the allocator, or hosts whose memory budget is fixed up
-// front.  ldpc_decode allocates the frame-state slots of its global-memory
-// form (cudaMallocAsync) and uploads a code on its first use on a device
-// (cudaMalloc); this entry point does neither.  It runs the same
+// Some callers cannot allocate device memory at the moment they decode:
+// real-time loops that must not enter the CUDA allocator (its calls can block
+// on the device or take locks for an unbounded time), processes whose device
+// memory is all handed out up front to another allocator (a framework's
+// caching pool) or capped by a fixed budget, and plug-ins that run inside a
+// host application which owns every allocation.  ldpc_decode allocates the
+// frame-state slots of its global-memory form (cudaMallocAsync) and uploads a
+// code on its first use on a device (cudaMalloc); this entry point does
+// neither.  It runs the same
 // global-memory-form kernels on a file-scope device array of fixed size,
 // holding the code's graph tables (copied from the host handle at each call)
 // followed by the state slots.
@@ -165,8 +167,12 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
 
   // state slots after the graph, as many as fit (at most the usual count)
   int sms = 1, optin = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(LDPC_ERR_CUDA, std::string("cudaDeviceGetAttribute(SM count): ") + cudaGetErrorString(e));
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess)
+    return fail(LDPC_ERR_CUDA, std::string("cudaDeviceGetAttribute(shared memory): ") + cudaGetErrorString(e));
+  if (sms < 1) sms = 1;
   size_t per, cta_fixed = 0;
   int fpc = 1;
   int64_t want;

@@ -193,7 +193,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
 
   // ---- schedule loop
   constexpr bool kLMDR = SCHED == kLMDRBP || SCHED == kSLMDRBP;
-  int64_t count = 0;
+  int64_t count = 0, nfall = 0;
   int nstar = 0;
   int enext = -1;  // LMDRBP: edge found by Alg. 2 line 9 for the next update (-1: none)
   bool stop = (a.check_interval > 0 && unsat == 0);
@@ -222,6 +222,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
       if (fallback) {  // Alg. 1 line 6
         eglob = global_argmax_R<A>(M, s);
         nstar = g.evn(eglob);
+        ++nfall;
       }
     }
     // lane k < d_v owns the k-th edge into n* (d_v <= 32 for this form)
@@ -375,9 +376,14 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     if (io.hard) io.hard[n] = (uint8_t)(s.L[n] < (L_)0);
     if (io.llr_out) io.llr_out[n] = (float)s.L[n];
   }
+  for (int e = lane; e < E; e += 32) {
+    if (io.c2v_out) io.c2v_out[e] = (float)s.C[e];
+    if (io.pre_out) io.pre_out[e] = (float)s.P[e];
+  }
   if (lane == 0) {
     if (io.updates) *io.updates = count;
     if (io.converged) *io.converged = unsat == 0 ? 1 : 0;
+    if (io.fallbacks) *io.fallbacks = nfall;
   }
   __syncwarp();
 }
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(32) se_queue_kernel(const QueueArgs q) {
       cur = it.code;
     }
     const int elem = A == kINT6 ? 1 : 4;
-    FrameIO io;
+    FrameIO io = empty_io();
     io.llr = (const unsigned char*)q.a.llr + it.llr_offset * elem;
     io.hard = q.a.hard ? q.a.hard + it.out_offset : nullptr;
     io.llr_out = nullptr;

@@ -64,6 +64,9 @@ struct DecodeArgs {
   uint8_t* converged;
   int32_t* trace;
   float* llr_out;
+  float* c2v_out;      // [batch][E] final L^C, or null
+  float* pre_out;      // [batch][E] final L~^C, or null
+  int64_t* fallbacks;  // [batch] CIRBP updates chosen by the residual fallback, or null
   int64_t max_updates;
   int64_t check_interval;
   float gamma_f;    // FP32 threshold on D
@@ -94,9 +97,29 @@ struct FrameIO {
   int64_t* updates;    // update count, or null
   uint8_t* converged;  // flags, or null
   int32_t* trace;      // max_updates edge ids, or null
+  float* c2v_out;      // E final L^C, or null
+  float* pre_out;      // E final L~^C, or null
+  int64_t* fallbacks;  // CIRBP fallback count, or null
   int64_t max_updates;
   uint64_t frame;  // global frame index (Algorithm 4's Philox counter)
 };
+
+// FrameIO with every optional output absent (queue form)
+inline __device__ FrameIO empty_io() {
+  FrameIO io;
+  io.llr = nullptr;
+  io.hard = nullptr;
+  io.llr_out = nullptr;
+  io.updates = nullptr;
+  io.converged = nullptr;
+  io.trace = nullptr;
+  io.c2v_out = nullptr;
+  io.pre_out = nullptr;
+  io.fallbacks = nullptr;
+  io.max_updates = 0;
+  io.frame = 0;
+  return io;
+}
 
 inline __host__ __device__ int align16(int x) { return (x + 15) & ~15; }
 
@@ -116,6 +139,9 @@ inline __device__ FrameIO batch_io(const DecodeArgs& a, int64_t b, int elem_byte
   io.updates = a.updates ? a.updates + b : nullptr;
   io.converged = a.converged ? a.converged + b : nullptr;
   io.trace = a.trace ? a.trace + b * a.max_updates : nullptr;
+  io.c2v_out = a.c2v_out ? a.c2v_out + b * (int64_t)a.g.E : nullptr;
+  io.pre_out = a.pre_out ? a.pre_out + b * (int64_t)a.g.E : nullptr;
+  io.fallbacks = a.fallbacks ? a.fallbacks + b : nullptr;
   io.max_updates = a.max_updates;
   io.frame = a.frame_offset + (uint64_t)b;
   return io;

@@ -23,6 +23,16 @@ NEAR_TIE = 1e-5
 _codes = {}
 
 
+class Spec(tuple):
+    """(check_idx, var_idx, M, N, K, punct) of a test code.  Codes lifted from a
+    protograph also carry the protograph (`base`, `Z`, `punct_cols`): the
+    library builds them through ldpc_code_build_qc, whose protograph view is
+    what the decode kernels of the benchmark read."""
+    base = None
+    Z = None
+    punct_cols = None
+
+
 def regular96():
     if "reg" not in _codes:
         c, v, m = wl.regular_code(96, 3, 6, 1)
@@ -38,11 +48,29 @@ def qc(which, Z):
         c, v = oracle.qc_lift(base, Z)
         M, N = base.shape[0] * Z, base.shape[1] * Z
         punct = d.punct_mask(Z) if d.punct_cols else None
-        _codes[key] = (c, v, M, N, d.info_cols * Z, punct)
+        s = Spec((c, v, M, N, d.info_cols * Z, punct))
+        s.base, s.Z, s.punct_cols = base, Z, list(d.punct_cols)
+        _codes[key] = s
     return _codes[key]
 
 
 def make_code(spec):
+    """The library's handle of a test code: through ldpc_code_build_qc for a
+    lifted code (checked to hold the oracle's edge set), else through
+    ldpc_code_create."""
+    c, v, m, n, k, punct = spec
+    if getattr(spec, "base", None) is None:
+        return L.Code.from_edges(c, v, m, n, k, punct)
+    code = L.Code.from_protograph(spec.base, spec.Z, k, spec.punct_cols or None)
+    assert code.info.qc_lifting == spec.Z, "no protograph view"
+    gc, gv = code.edges()
+    order = np.lexsort((v, c))
+    assert np.array_equal(gc, c[order]) and np.array_equal(gv, v[order]), "lift differs from the oracle's"
+    return code
+
+
+def make_code_edges(spec):
+    """The same code through ldpc_code_create (CSR tables, no protograph view)."""
     c, v, m, n, k, punct = spec
     return L.Code.from_edges(c, v, m, n, k, punct)
 
@@ -60,8 +88,8 @@ def llrs(spec, batch, ebn0, seed):
 
 def run_gpu(code, x, torch, **kw):
     dev = torch.device("cuda:0")
-    out = L.decode(code, torch.from_numpy(np.ascontiguousarray(x)).to(dev), want_trace=True,
-                   want_llr=True, **kw)
+    kw.setdefault("want_trace", True)
+    out = L.decode(code, torch.from_numpy(np.ascontiguousarray(x)).to(dev), want_llr=True, **kw)
     torch.cuda.synchronize()
     return {k: t.cpu().numpy() for k, t in out.items()}
 

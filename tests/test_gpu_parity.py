@@ -7,8 +7,8 @@ import oracle
 import paper_2102_11089_gb300 as L
 from paper_2102_11089_gb300 import workloads as wl
 
-from gpu_helpers import (assert_bitexact, fer_in_interval, llrs, make_code, qc, regular96, run_gpu,
-                         run_oracle, trace_prefix_ok, within_tol)
+from gpu_helpers import (assert_bitexact, fer_in_interval, llrs, make_code, make_code_edges, qc, regular96,
+                         run_gpu, run_oracle, trace_prefix_ok, within_tol)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -109,21 +109,90 @@ def test_int6_bitexact_bg2_degree1_and_punctured(schedule):
     assert_bitexact(g, o, schedule)
 
 
+@pytest.mark.parametrize("which,Z", [("wifi", 96), ("bg2", 16)])
+@pytest.mark.parametrize("schedule", ALL)
+@pytest.mark.parametrize("arith", ["int6", "fp32"])
+def test_protograph_view_equals_csr_tables(which, Z, schedule, arith):
+    # the same lifted code built from its protograph (neighbours and edge ids
+    # computed from the circulant shifts) and from its edge list (CSR tables):
+    # every output identical, FP32 included (same arithmetic in the same order)
+    spec = qc(which, Z)
+    code_qc, code_tab = make_code(spec), make_code_edges(spec)
+    assert code_qc.info.qc_lifting == Z and code_tab.info.qc_lifting == 0
+    lam = llrs(spec, 24, 1.25, 606)
+    x = wl.quantize_llrs(lam, 0.5) if arith == "int6" else lam
+    kw = dict(schedule=schedule, max_updates=2 * code_qc.E, gamma=0.1, n_p=16, n_g=16, seed=21)
+    a = run_gpu(code_qc, x, torch, arith=arith, **kw)
+    b = run_gpu(code_tab, x, torch, arith=arith, **kw)
+    for k in ["hard", "updates", "converged", "llr", "trace"]:
+        assert np.array_equal(a[k], b[k]), k
+
+
 # ---------------------------------------------------------------------------
 # FP32 sum-product: tolerance, trace prefix, FER interval
 
 
-@pytest.mark.parametrize("which", ["reg", "wifi"])
-@pytest.mark.parametrize("iters", [1, 2])
+@pytest.mark.parametrize("which", ["reg", "wifi", "bg2"])
+@pytest.mark.parametrize("iters", [1, 2, 5])
 def test_fp32_flooding_messages_within_tolerance(which, iters):
-    spec = regular96() if which == "reg" else qc("wifi", 96)
+    # every C2V message of flooding iteration `iters` (and the total LLRs) within
+    # 1e-4 max(1, |m|) of the FP64 oracle's
+    spec = regular96() if which == "reg" else (qc("wifi", 96) if which == "wifi" else qc("bg2", 16))
     code = make_code(spec)
     lam = llrs(spec, 32, 1.5, 5)
     kw = dict(schedule="flooding", max_updates=iters * code.E, check_interval=0)
-    g = run_gpu(code, lam, torch, arith="fp32", **kw)
-    o = run_oracle(spec, lam, "fp32", **kw)
+    g = run_gpu(code, lam, torch, arith="fp32", want_msgs=True, want_trace=False, **kw)
+    o = oracle_state(spec, lam, "fp32", **kw)
+    ok = within_tol(g["c2v"], o["state"]["C"])
+    assert ok.all(), f"{(~ok).sum()} messages, max |d| {np.max(np.abs(g['c2v'] - o['state']['C']))}"
     ok = within_tol(g["llr"], o["llr"])
     assert ok.all(), f"max excess {np.max(np.abs(g['llr'] - o['llr']))}"
+
+
+def oracle_state(spec, x, arith, **kw):
+    c, v, m, n, k, punct = spec
+    if arith == "int6":
+        return oracle.decode(c, v, m, n, qllr=x, want_trace=True, want_state=True, threads=8, **kw)
+    return oracle.decode(c, v, m, n, llr=x.astype(np.float64), want_trace=True, want_state=True, threads=8, **kw)
+
+
+@pytest.mark.parametrize("schedule", ALL)
+@pytest.mark.parametrize("which", ["reg", "bg2"])
+def test_int6_final_message_state_bitexact(which, schedule):
+    # the whole final message state (L^C and, for the dynamic schedules, L~^C),
+    # not only the decisions, equals the oracle's; CIRBP also its fallback count
+    spec = regular96() if which == "reg" else qc("bg2", 16)
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 40, 1.25, 808), 0.5)
+    kw = dict(schedule=schedule, max_updates=2 * code.E, gamma=0.2, n_p=8, n_g=8, seed=7)
+    g = run_gpu(code, q, torch, arith="int6", want_msgs=True, want_fallbacks=True, **kw)
+    o = oracle_state(spec, q, "int6", **kw)
+    assert_bitexact(g, o, schedule)
+    assert np.array_equal(g["c2v"], o["state"]["C"])
+    if schedule != "flooding":
+        assert np.array_equal(g["pre"], o["state"]["P"])
+    assert np.array_equal(g["fallbacks"], o["counters"]["fallback"])
+    if schedule == "cirbp":
+        assert g["fallbacks"].sum() > 0
+
+
+@pytest.mark.parametrize("schedule", ["cirbp", "lmd-cirbp", "me-lmd-cirbp", "rbp"])
+def test_fp32_message_state_before_first_near_tie(schedule):
+    # frames whose oracle run meets no near-tie: same trace, and every final
+    # message within 1e-4 max(1, |m|) of the oracle's
+    spec = qc("wifi", 96)
+    code = make_code(spec)
+    lam = llrs(spec, 48, 1.5, 4711)
+    T = 256
+    kw = dict(schedule=schedule, max_updates=T, check_interval=0, gamma=0.1, n_p=16, n_g=16, seed=3)
+    g = run_gpu(code, lam, torch, arith="fp32", want_msgs=True, want_fallbacks=True, **kw)
+    o = oracle_state(spec, lam, "fp32", **kw)
+    clean = (o["gap"][:, :T] >= 1e-5).all(1)
+    assert clean.sum() >= 8, clean.sum()
+    assert np.array_equal(g["trace"][clean, :T], o["trace"][clean, :T])
+    assert within_tol(g["c2v"][clean], o["state"]["C"][clean]).all()
+    assert within_tol(g["pre"][clean], o["state"]["P"][clean]).all()
+    assert np.array_equal(g["fallbacks"][clean], o["counters"]["fallback"][clean])
 
 
 @pytest.mark.parametrize("schedule", DYN)

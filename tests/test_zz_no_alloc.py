@@ -1,7 +1,10 @@
 """ldpc_decode_noalloc, the entry point for callers that must not allocate
-(e.g. while their stream is captured into a CUDA graph): through the C ABI its
-outputs must equal those of ldpc_decode, on two calls in a row (the second call
-finds the first call's leftovers in the shared static array).  This file is
+device memory when they decode (real-time loops kept out of the CUDA allocator,
+processes whose memory belongs to another allocator or to a fixed budget):
+through the C ABI its outputs must equal those of ldpc_decode, on two calls in
+a row (the second call finds the first call's leftovers in the shared static
+array), and in 6-bit mode equal the oracle's bit for bit.  Lifted codes run the
+protograph-view kernels, edge-list codes the CSR-table kernels.  This file is
 collected last on purpose."""
 import numpy as np
 import pytest
@@ -9,7 +12,7 @@ import pytest
 import paper_2102_11089_gb300 as L
 from paper_2102_11089_gb300 import workloads as wl
 
-from gpu_helpers import llrs, make_code, qc, regular96, within_tol
+from gpu_helpers import assert_bitexact, llrs, make_code, make_code_edges, qc, regular96, run_oracle, within_tol
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -32,13 +35,17 @@ def _outputs(B, N, budget, dev):
 
 
 CASES = [("reg", "lmd-cirbp", "int6"), ("reg", "cirbp", "fp32"), ("wifi", "me-lmd-cirbp", "fp32"),
-         ("wifi", "me-cirbp", "int6"), ("bg2", "flooding", "fp32"), ("bg2", "rbp", "int6")]
+         ("wifi", "me-cirbp", "int6"), ("wifi", "me-lmd-cirbp", "int6"), ("bg2", "flooding", "fp32"),
+         ("bg2", "flooding", "int6"), ("bg2", "rbp", "int6"), ("bg2", "lmd-cirbp", "fp32"),
+         ("wifi-tab", "me-lmd-cirbp", "int6")]
 
 
 @pytest.mark.parametrize("which,schedule,arith", CASES)
 def test_noalloc_matches_decode_on_two_calls(which, schedule, arith):
-    spec = regular96() if which == "reg" else (qc("wifi", 96) if which == "wifi" else qc("bg2", 16))
-    code = make_code(spec)
+    spec = {"reg": regular96, "wifi": lambda: qc("wifi", 96), "wifi-tab": lambda: qc("wifi", 96),
+            "bg2": lambda: qc("bg2", 16)}[which]()
+    code = make_code_edges(spec) if which == "wifi-tab" else make_code(spec)
+    assert (code.info.qc_lifting > 0) == (which in ("wifi", "bg2"))
     dev = torch.device("cuda:0")
     lam = llrs(spec, 40, 1.5, 314)
     x = wl.quantize_llrs(lam, 0.5) if arith == "int6" else lam
@@ -52,6 +59,10 @@ def test_noalloc_matches_decode_on_two_calls(which, schedule, arith):
         for k in ["hard", "updates", "converged", "trace"]:
             assert torch.equal(out[k], ref[k]), (call, k)
         assert within_tol(out["llr"].cpu().numpy(), ref["llr"].cpu().numpy().astype(np.float64)).all()
+    if arith == "int6":
+        kw = dict(schedule=schedule, max_updates=budget, n_p=16, n_g=8, seed=11, gamma=0.1)
+        o = run_oracle(spec, x.cpu().numpy(), "int6", **kw)
+        assert_bitexact({k: v.cpu().numpy() for k, v in out.items()}, o, schedule)
 
 
 def test_noalloc_rejects_state_beyond_static_scratch():
