@@ -529,3 +529,73 @@ def test_regular_code_has_girth_at_least_six():
     ov = H @ H.T
     np.fill_diagonal(ov, 0)
     assert ov.max() <= 1
+
+
+# ---------------------------------------------------------------------------
+# Multi-edge steps (Alg. 4, 5, 6) on a hand-derived toy graph
+
+
+def _me_golden(golden_dir):
+    with open(os.path.join(golden_dir, "me_toy_steps.json")) as f:
+        return json.load(f)
+
+
+def _me_run(g, schedule, budget):
+    H = np.array(g["H"])
+    chk, var = np.nonzero(H)  # row-major: (check, variable) order = the edge ids
+    q = np.array([g["q"]], dtype=np.int8)
+    return oracle.decode(chk.astype(np.int32), var.astype(np.int32), H.shape[0], H.shape[1], qllr=q,
+                         schedule=schedule, n_p=g["n_p"], n_g=g["n_g"], q_step=g["q_step"],
+                         max_updates=budget, check_interval=0, want_trace=True, want_state=True)
+
+
+def _me_check_state(o, want):
+    for k in ("C", "P", "L", "Lt", "D"):
+        assert o["state"][k][0].tolist() == [float(x) for x in want[k]], k
+
+
+def test_me_toy_table_and_initial_selection(golden_dir):
+    g = _me_golden(golden_dir)
+    for k, expr in g["T"].items():  # the integer CI table of the hand derivation
+        assert eval(expr, {"round": round, "tanh": math.tanh}) == {1: 8025, 2: 15142, 3: 20812, 4: 24955,
+                                                                     5: 27796}[int(k)]
+    D = np.array(g["init"]["D"], dtype=np.float64)
+    assert [min(int(d) * 8 // 65534, 7) for d in D] == g["init"]["groups"]
+    sel, _ = oracle.alg4(D, np.ones(6, np.uint8), g["n_g"], g["n_p"], arith=oracle.INT)
+    assert sel.tolist() == g["init"]["selected"]
+
+
+@pytest.mark.parametrize("schedule", ["me-cirbp", "me-lmd-cirbp"])
+def test_me_toy_first_step(golden_dir, schedule):
+    # Alg. 5 / Alg. 6 line 5 on P = {2, 4, 5}: per-p residual argmax on the
+    # pre-step state, all commits, then the refresh of checks c0 and c2
+    g = _me_golden(golden_dir)
+    o = _me_run(g, schedule, 3)
+    want = g["after_step1"]
+    assert o["updates"][0] == 3
+    assert o["trace"][0].tolist() == want["trace"]
+    _me_check_state(o, want)
+    assert [min(int(d) * 8 // 65534, 7) for d in o["state"]["D"][0]] == want["groups"]
+
+
+def test_me_lmd_toy_second_selection_and_step(golden_dir):
+    # Alg. 6 lines 6-14: P' = {argmax_{U(m*_p, p)} D} = {1, 4} (p = 2 and p = 5 both
+    # name VN 4; p = 4 has degree 1), top-up of N_P - |P'| = 1 VN over O_N \ P'
+    # gives {3}; the second step commits on {1, 3, 4}
+    g = _me_golden(golden_dir)
+    o = _me_run(g, "me-lmd-cirbp", 6)
+    want = g["me_lmd_cirbp"]["after_step2"]
+    assert o["trace"][0].tolist() == want["trace"]
+    H = np.array(g["H"])
+    chk, var = np.nonzero(H)
+    assert sorted(var[o["trace"][0][3:6]].tolist()) == g["me_lmd_cirbp"]["selected_step2"]
+    _me_check_state(o, want)
+
+
+def test_me_cirbp_toy_second_step(golden_dir):
+    # Alg. 5: the second selection is Alg. 4 over O_N again: {0, 3, 4}
+    g = _me_golden(golden_dir)
+    o = _me_run(g, "me-cirbp", 6)
+    want = g["me_cirbp"]["after_step2"]
+    assert o["trace"][0].tolist() == want["trace"]
+    _me_check_state(o, want)
