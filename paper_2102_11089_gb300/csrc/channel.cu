@@ -10,25 +10,11 @@
 // r sin(2 pi u_b).  One thread per Philox block, grid-stride; the 6-bit
 // quantiser clamp(rint(lambda / step), -31, 31) runs in the same pass.
 #include "internal.h"
+#include "philox.cuh"
 
 namespace ldpc {
 
 namespace {
-
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-}
 
 // -ln(u) * 2 with u = (x + 1/2) 2^-32, accurate near u = 1 as well
 __device__ __forceinline__ float minus2_log_u(uint32_t x) {

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "device_math.cuh"
+#include "philox.cuh"
 
 namespace ldpc {
 
@@ -193,22 +194,6 @@ struct MEState {
   float fx, ifx;     // FP32 fixed point: 2^k and 2^-k
 };
 
-__device__ __forceinline__ void philox4(uint32_t c[4], uint64_t seed) {
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-}
-
 template <class X>
 __device__ __forceinline__ float ci_me(const MEState<kFP32, X>&, float a, float b) { return ci_fp(a, b); }
 template <class X>
@@ -316,7 +301,7 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
       }
       if (!fill) continue;
       uint32_t w[4] = {(uint32_t)q, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
-      if (fm) philox4(w, seed);
+      if (fm) philox4x32_10(w, seed);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const bool c = ((fm >> i) & 1u) && w[i] <= thr;
