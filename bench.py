@@ -2,9 +2,10 @@
 on one GB300, next to flooding BP at equal FER and the CPU oracle.
 
 Workload (default): the WiFi-like rate-1/2 QC code (12x24 protograph, Z=96,
-n=2304, E=7776, k=1152), BPSK/AWGN at Eb/N0 = 2.0 dB, FP32 sum-product,
-ME-LMD-CIRBP (Algorithm 6) with N_P = 64, N_G = 16, budget 5 iteration
-equivalents (5E committed messages), syndrome checked after every step.
+n=2304, E=7776, k=1152), BPSK/AWGN at Eb/N0 = 1.5 dB, FP32 sum-product,
+ME-LMD-CIRBP (Algorithm 6) with N_P = 64, N_G = 16, budget 3 iteration
+equivalents (3E committed messages: the I_max = 3 regime of Sec. 5, where the
+frame error rate is above zero), syndrome checked after every step.
 One step = channel kernel (Philox AWGN LLRs) + decode of one batch of 65,536
 frames; LLR inputs (604 MB) exceed L2.  The end-to-end figure (`e2e`) decodes
 batches copied from pinned host memory each step and reads the decisions back.
@@ -39,8 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--schedule", default="me-lmd-cirbp")
     ap.add_argument("--batch", type=int, default=65536)
-    ap.add_argument("--ebn0", type=float, default=2.0)
-    ap.add_argument("--budget-iters", type=float, default=5.0)
+    ap.add_argument("--ebn0", type=float, default=1.5)
+    ap.add_argument("--budget-iters", type=float, default=3.0)
     ap.add_argument("--n-p", type=int, default=64)
     ap.add_argument("--n-g", type=int, default=16)
     ap.add_argument("--arith", default="fp32")
@@ -60,6 +61,10 @@ def parse():
                     help="run only the weighted-BP forward/adjoint timing and print its JSON")
     ap.add_argument("--large-only", action="store_true",
                     help="run only the BG1-shaped cluster / global-memory comparison and print its JSON")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="leave out the Eb/N0 x N_P x budget sweep and the gamma sweep (extras)")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="run only the Eb/N0 x N_P x budget sweep and the gamma sweep and print their JSON")
     return ap.parse_args()
 
 
@@ -139,24 +144,20 @@ class Clocks:
 
 
 def bytes_per_update(code, arith):
-    """Shared-memory bytes of one committed C2V update, from the per-update
-    work of Table I with the code's average degrees (dv, dc):
-      CN selection   2 msg reads on each of the dv edges into n*
-      commit         read L~^C, write L^C, read/write L_n*, write D_n*
-      V2C inputs     (dv-1) refreshed checks x dc edges: read L_j and L^C
-      C2V outputs    (dv-1)(dc-1) writes of L~^C
-      CI update      (dv-1)(dc-1) x (dv reads of L~^C + L_j + lambda_j, write L~_j, D_j)
-    """
-    m = 4 if arith == "fp32" else 1
-    l = 4 if arith == "fp32" else 2
+    """Algorithmic shared-memory bytes of one committed C2V update (FP32 state,
+    V2C derived as L_j - L^C), from the per-update work of Table I with the
+    code's average degrees (dv, dc):
+      CN selection   8 dv       (L~^C and L^C of the dv edges into n*)
+      commit         16         (read L~^C, write L^C, read/write L_n*)
+      refresh        (dv-1) [8 dc + 8 (dc-1)]   (V2C inputs L_j, L^C; old/new L~^C)
+      CI update      (dv-1)(dc-1) 12            (read/write L~_j, write D_j)
+    with m = 4-byte messages and l = 4-byte LLRs / metrics; 6-bit mode: m = 1,
+    l = 2 in the same terms."""
     dv = code.E / code.N
     dc = code.E / code.M
-    sel = 2 * m * dv
-    commit = 2 * m + 3 * l
-    v2c = (dv - 1) * dc * (l + m)
-    c2v = (dv - 1) * (dc - 1) * m
-    ci = (dv - 1) * (dc - 1) * (dv * m + 2 * l + 2 * l)
-    return sel + commit + v2c + c2v + ci
+    m, l = (4, 4) if arith == "fp32" else (1, 2)
+    return (2 * m * dv + (2 * m + 2 * l) + (dv - 1) * ((l + m) * dc + 2 * m * (dc - 1))
+            + (dv - 1) * (dc - 1) * 3 * l)
 
 
 def kernel_digest():
@@ -175,7 +176,7 @@ def profiled_traffic(args, batch):
     import re
     path = os.path.join(ROOT, "profiles", "me_decode_kernel_wifi_n2304_fp32.md")
     if not os.path.exists(path) or args.schedule != "me-lmd-cirbp" or args.arith != "fp32" or \
-            args.n_p != 64 or args.n_g != 16 or args.ebn0 != 2.0 or args.budget_iters != 5.0:
+            args.n_p != 64 or args.n_g != 16 or args.ebn0 != 1.5 or args.budget_iters != 3.0:
         return None, None
     text = open(path).read()
     m = re.search(r"digest \(decode_me.cu,\s+device_math.cuh, graph.cuh\): ([0-9a-f]{12})", text)
@@ -184,6 +185,33 @@ def profiled_traffic(args, batch):
     if not m or not t or m.group(1) != kernel_digest():
         return None, None
     return float(t.group(1)) * 1e6 * batch / 65536, (float(i.group(1)) if i else None)
+
+
+def measured_smem_peak(L, device, stream):
+    """Shared-memory read bandwidth (GB/s) of the ldpc_smem_stream kernel: best of
+    a few launch shapes (CTAs per SM x threads), each timed with CUDA events on
+    the launching stream after a warm-up launch."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    best = 0.0
+    shapes = []
+    for per_sm, threads in ((2, 1024), (4, 512), (8, 256)):
+        blocks = sms * per_sm
+        sink = torch.empty(blocks * threads, dtype=torch.int32, device=device)
+        iters = 4096
+        L.smem_stream(blocks, threads, iters, sink, stream=stream)
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nbytes = L.smem_stream(blocks, threads, iters, sink, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        gbs = nbytes / (min(ts) * 1e-3) / 1e9
+        shapes.append({"ctas_per_sm": per_sm, "threads": threads, "gb_s": gbs, "ms": min(ts)})
+        best = max(best, gbs)
+    return best, shapes
 
 
 def measured_peaks():
@@ -403,14 +431,18 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(device)
     sm_count = props.multi_processor_count
     clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    smem_peak = sm_count * SMEM_BYTES_PER_CLK_PER_SM * clk_mhz * 1e6 / 1e9
+    smem_derived = sm_count * SMEM_BYTES_PER_CLK_PER_SM * clk_mhz * 1e6 / 1e9
+    smem_peak, smem_shapes = measured_smem_peak(L, device, stream)
     traffic, issue_pct = profiled_traffic(args, B)
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
                 "frac": achieved / smem_peak, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch (ncu, 16,384-frame capture scaled by frames); "
                                 "the bound is shared memory, DRAM carries only LLRs in and decisions out",
-                "peak_source": f"derived: {sm_count} SMs x 128 B/clk x median SM clock "
-                               f"{clk_mhz:.0f} MHz (shared memory is not in MEASURED_PEAKS)",
+                "peak_source": "measured: ldpc_smem_stream (conflict-free 128-bit ld.shared over every SM, "
+                               "CUDA events, best launch shape); shared memory is not in MEASURED_PEAKS",
+                "peak_shapes": smem_shapes,
+                "peak_derived_gbs": smem_derived,
+                "peak_derived_note": f"{sm_count} SMs x 128 B/clk x median SM clock {clk_mhz:.0f} MHz",
                 "kernel": f"me_decode_kernel ({args.schedule}, {args.arith})",
                 "bytes_per_update": bpu, "updates_per_launch": upd_total / args.steps,
                 "launch_ms": dec_avg, "hbm_peak_gbs": peaks.get("hbm_gbs"), "peaks": peaks_kind,
@@ -479,7 +511,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         extras = run_extras(args, L, code, device, stream, fer, budget, value)
 
-    # launches: channel + decode per step
+    # launches in the timed region: channel + decode per step
     launches = 2 * args.steps
     cpu = None
     if rank == 0 and world == 1:
@@ -546,6 +578,9 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
     ms_se, o_se = time_decode(L, code, x[:B3].contiguous(), p_se, reps=1)
     res["single_edge_lmd_cirbp"] = {"frames": B3, "fer": fer_of(o_se), "ms": ms_se,
                                     "gbit_s": B3 * code.K / (ms_se * 1e-3) / 1e9}
+    if not args.no_sweep:
+        res["sweep_config2"] = run_sweep(args, L, code, device)
+        res["gamma_sweep_cirbp"] = run_gamma_sweep(args, L, code, device)
     if args.queue_frames > 0:
         res["queue_mixed_bg2"] = run_queue_mixed(args, L, device)
     if args.large_frames > 0:
@@ -561,6 +596,107 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
                                      "J": [clean(J[k]) for k in range(3)], "F": [clean(F[k]) for k in range(3)],
                                      "incorrect_per_iteration": [int(cnt[k][:, 1].sum()) for k in range(3)]}
     return res
+
+
+def clopper_pearson(k, n, alpha=0.05):
+    from scipy import stats
+    lo = 0.0 if k == 0 else float(stats.beta.ppf(alpha / 2, k, n - k + 1))
+    hi = 1.0 if k == n else float(stats.beta.ppf(1 - alpha / 2, k + 1, n - k))
+    return lo, hi
+
+
+def frame_errors(out):
+    return int((out["hard"].sum(1) > 0).sum().item())
+
+
+def run_sweep(args, L, code, device, ebn0s=(1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5), nps=(4, 16, 64),
+              budgets=(1, 2, 3, 5), frames=65536, frames_np4=16384):
+    """The WiFi-like code over Eb/N0 x N_P x budget (ME-LMD-CIRBP, FP32), each
+    point against flooding BP at equal FER on the same frames.
+
+    Flooding's FER after I iterations follows from one run of 50 iterations
+    that stops each frame at its first zero syndrome: a frame is decoded
+    correctly within I iterations iff it stopped by iteration I on the all-zero
+    word (its run up to then is the same at any budget >= I).  The equal-FER
+    iteration count I* is the smallest I whose FER is at most the CI FER; its
+    throughput is timed by a run at budget I*E.  Also reported: flooding's FER
+    at the CI budget itself (the same number of committed messages)."""
+    import torch
+    E, K = code.E, code.K
+    rows = []
+    flood_ms_cache = {}
+    t_start = time.perf_counter()
+    for eb in ebn0s:
+        B = frames
+        ebt = torch.full((B,), eb, dtype=torch.float32, device=device)
+        llr, _ = L.awgn_llr(code, ebt, seed=4242, frame_offset=0)
+        pf = L.make_params("flooding", "fp32", max_updates=50 * E, check_interval=E)
+        of = L.decode(code, llr, pf)
+        torch.cuda.synchronize()
+        it_used = (of["updates"] // E).cpu().numpy()
+        ok = ((of["hard"].sum(1) == 0) & ((of["converged"] & 1) == 1)).cpu().numpy()
+        flood_fer = [1.0 - float(np.mean(ok & (it_used <= i))) for i in range(0, 51)]
+        for n_p in nps:
+            Bn = frames_np4 if n_p <= 4 else frames
+            x = llr[:Bn]
+            for bi in budgets:
+                p = L.make_params("me-lmd-cirbp", "fp32", gamma=0.1, n_p=n_p, n_g=16, max_updates=bi * E,
+                                  check_interval=1, seed=1234)
+                ms, o = time_decode(L, code, x, p, reps=1)
+                errs = frame_errors(o)
+                fer = errs / Bn
+                lo, hi = clopper_pearson(errs, Bn)
+                fsub = [1.0 - float(np.mean((ok & (it_used <= i))[:Bn])) for i in range(0, 51)]
+                istar = next((i for i in range(1, 51) if fsub[i] <= fer), None)
+                row = {"ebn0_db": eb, "n_p": n_p, "budget_iters": bi, "frames": Bn, "ci_fer": fer,
+                       "ci_fer_ci95": [lo, hi], "ci_ms": ms, "ci_gbit_s": Bn * K / (ms * 1e-3) / 1e9,
+                       "ci_mean_updates": float(o["updates"].float().mean().item()),
+                       "flood_fer_same_budget": fsub[bi]}
+                if istar is None:
+                    row["flood_equal_fer"] = {"reached": False, "flood_fer_50": fsub[50]}
+                else:
+                    key = (eb, Bn, istar)
+                    if key not in flood_ms_cache:
+                        pfi = L.make_params("flooding", "fp32", max_updates=istar * E, check_interval=E)
+                        flood_ms_cache[key] = time_decode(L, code, x, pfi, reps=1)[0]
+                    fms = flood_ms_cache[key]
+                    fg = Bn * K / (fms * 1e-3) / 1e9
+                    row["flood_equal_fer"] = {"iterations": istar, "fer": fsub[istar], "ms": fms, "gbit_s": fg}
+                    row["ci_over_flood"] = row["ci_gbit_s"] / fg
+                rows.append(row)
+        del llr, of
+    return {"workload": "wifi-like n2304, ME-LMD-CIRBP FP32, N_G 16, Eb/N0 x N_P x budget; flooding at equal "
+                        "FER on the same frames", "points": rows, "seconds": time.perf_counter() - t_start}
+
+
+def run_gamma_sweep(args, L, code, device, gammas=(0.0, 0.05, 0.1, 0.15, 0.2, 0.25, 0.3), frames=8192,
+                    ebn0=1.5, budget_iters=3):
+    """CIRBP (Algorithm 1) over the CI threshold gamma on the WiFi-like code:
+    FER and kappa = Pr(D_{n*} < gamma), the share of updates whose edge came
+    from the residual fallback (Sec. 5.A), with the decode throughput."""
+    import torch
+    E, K = code.E, code.K
+    ebt = torch.full((frames,), ebn0, dtype=torch.float32, device=device)
+    llr, _ = L.awgn_llr(code, ebt, seed=5151, frame_offset=0)
+    rows = []
+    for gmm in gammas:
+        p = L.make_params("cirbp", "fp32", gamma=gmm, max_updates=budget_iters * E, check_interval=1)
+        L.decode(code, llr, p)  # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        o = L.decode(code, llr, p, want_fallbacks=True)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        errs = frame_errors(o)
+        upd = int(o["updates"].sum().item())
+        fb = int(o["fallbacks"].sum().item())
+        rows.append({"gamma": gmm, "fer": errs / frames, "fer_ci95": list(clopper_pearson(errs, frames)),
+                     "kappa": fb / max(1, upd), "mean_updates": upd / frames, "ms": ms,
+                     "gbit_s": frames * K / (ms * 1e-3) / 1e9})
+    return {"workload": f"wifi-like n2304, CIRBP FP32, Eb/N0 {ebn0} dB, budget {budget_iters}E",
+            "frames": frames, "points": rows}
 
 
 QUEUE_ZS = (16, 32, 64, 128, 256, 384)
@@ -855,6 +991,17 @@ def main():
         return
     if args.decode_only:
         run_decode_only(args)
+        return
+    if args.sweep_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2102_11089_gb300 as L
+        design, Z = workload(args)
+        code = L.Code.from_protograph(design.shifts(Z), Z, design.info_cols * Z, design.punct_cols)
+        dev = torch.device("cuda", 0)
+        print(json.dumps({"sweep_config2": run_sweep(args, L, code, dev),
+                          "gamma_sweep_cirbp": run_gamma_sweep(args, L, code, dev)}))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -388,6 +388,18 @@ ldpc_status_t ldpc_ci_stats(const float *llr_now, const float *llr_pre, int64_t 
  * for a failed stream. */
 ldpc_status_t ldpc_sync(void *cuda_stream);
 
+/* Shared-memory read stream: the measured peak against which the decoders'
+ * shared-memory traffic is compared (their frame state lives in shared
+ * memory).  The paper has no counterpart; it is a measurement aid.  Launches
+ * `blocks` CTAs of `threads` threads (a multiple of 32, at most 1024) on
+ * `cuda_stream`; each thread issues `iters` x 4 conflict-free 128-bit loads
+ * from a 32 KB shared array and writes one folded word to sink[block *
+ * threads + thread] (device uint32, caller-owned).  *bytes (host, may be NULL)
+ * receives the bytes read: blocks x threads x iters x 64.  Time it with events
+ * on the same stream.  Errors: INVALID_ARG, CUDA. */
+ldpc_status_t ldpc_smem_stream(int32_t blocks, int32_t threads, int32_t iters, uint32_t *sink, int64_t *bytes,
+                               void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,7 @@ def _load():
             ("ldpc_decode", [P, P, I64, P, P, P, P, P, P, P]),
             ("ldpc_decode_noalloc", [P, P, I64, P, P, P, P, P, P, P]),
             ("ldpc_decode_ex", [P, P, I64, P, P, P]),
+            ("ldpc_smem_stream", [I32, I32, I32, P, P, P]),
             ("ldpc_decode_queue", [P, I32, P, I64, P, P, P, P, P, I32, P]),
             ("ldpc_wbp_forward", [P, P, I64, P, P, I64, P, ctypes.c_float, P, P, P, P]),
             ("ldpc_ci_stats", [P, P, I64, I32, P, P]),
@@ -338,6 +339,18 @@ def awgn_llr_codewords(code: Code, ebn0_db, codewords, seed: int, frame_offset: 
                                            None if qout is None else ctypes.c_void_p(qout.data_ptr()), q_step,
                                            _stream_ptr(stream)))
     return out, qout
+
+
+def smem_stream(blocks: int, threads: int, iters: int, sink, stream=None) -> int:
+    """ldpc_smem_stream: launch the shared-memory read stream on `stream`;
+    `sink` is a CUDA uint32/int32 tensor of blocks * threads words.  Returns the
+    bytes the launch reads."""
+    if sink.numel() < blocks * threads:
+        raise ValueError("sink too small")
+    nb = ctypes.c_int64(0)
+    _check(_load().ldpc_smem_stream(blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(nb),
+                                    _stream_ptr(stream)))
+    return int(nb.value)
 
 
 def sync(stream=None):

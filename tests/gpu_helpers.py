@@ -10,6 +10,7 @@ step whose oracle top-2 metric gap (relative to max(1, |metric|)) is below
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -19,6 +20,7 @@ from paper_2102_11089_gb300 import workloads as wl
 
 TOL_REL = 1e-4
 NEAR_TIE = 1e-5
+THREADS = max(1, os.cpu_count() or 1)
 
 _codes = {}
 
@@ -97,8 +99,8 @@ def run_gpu(code, x, torch, **kw):
 def run_oracle(spec, x, arith, **kw):
     c, v, m, n, k, punct = spec
     if arith == "int6":
-        return oracle.decode(c, v, m, n, qllr=x, want_trace=True, threads=8, **kw)
-    return oracle.decode(c, v, m, n, llr=x.astype(np.float64), want_trace=True, threads=8, **kw)
+        return oracle.decode(c, v, m, n, qllr=x, want_trace=True, threads=THREADS, **kw)
+    return oracle.decode(c, v, m, n, llr=x.astype(np.float64), want_trace=True, threads=THREADS, **kw)
 
 
 def assert_bitexact(g, o, schedule):

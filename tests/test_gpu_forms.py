@@ -6,8 +6,8 @@ import pytest
 import paper_2102_11089_gb300 as L
 from paper_2102_11089_gb300 import workloads as wl
 
-from gpu_helpers import (assert_bitexact, fer_in_interval, llrs, make_code, qc, regular96, run_gpu,
-                         run_oracle, trace_prefix_ok)
+from gpu_helpers import (NEAR_TIE, assert_bitexact, fer_in_interval, llrs, make_code, qc, regular96, run_gpu,
+                         run_oracle, trace_prefix_ok, within_tol)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -143,3 +143,27 @@ def test_cluster_form_bg1_z384_matches_oracle_int6():
     g = run_gpu(code, q, torch, arith="int6", form=L.FORM_CLUSTER, **kw)
     o = run_oracle(spec, q, "int6", **kw)
     assert_bitexact(g, o, "me-lmd-cirbp")
+
+
+def test_cluster_form_bg1_z384_fp32_matches_oracle():
+    # FP32 on the cluster form of the 26,112-bit code: the edge trace equals the
+    # oracle's up to its first near-tie; over the first steps (before any near-tie)
+    # every final message L^C, L~^C within 1e-4 max(1, |m|) of FP64
+    import oracle
+    spec = qc("bg1", 384)
+    code = make_code(spec)
+    c, v, m, n, k, punct = spec
+    lam = llrs(spec, 4, 1.2, 43)
+    kw = dict(schedule="me-lmd-cirbp", max_updates=code.E // 4, gamma=0.1, n_p=256, n_g=16, seed=8)
+    g = run_gpu(code, lam, torch, arith="fp32", form=L.FORM_CLUSTER, **kw)
+    o = run_oracle(spec, lam, "fp32", **kw)
+    lens = trace_prefix_ok(g, o)
+    assert lens.max() >= 256
+    kw["max_updates"] = 512
+    g = run_gpu(code, lam, torch, arith="fp32", form=L.FORM_CLUSTER, want_msgs=True, **kw)
+    o = oracle.decode(c, v, m, n, llr=lam.astype(np.float64), want_trace=True, want_state=True, threads=8, **kw)
+    clean = (o["gap"][:, :512] >= NEAR_TIE).all(1)
+    assert clean.sum() >= 1, o["gap"][:, :512].min(1)
+    assert np.array_equal(g["trace"][clean, :512], o["trace"][clean, :512])
+    assert within_tol(g["c2v"][clean], o["state"]["C"][clean]).all()
+    assert within_tol(g["pre"][clean], o["state"]["P"][clean]).all()
