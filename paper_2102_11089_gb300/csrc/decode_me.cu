@@ -109,7 +109,7 @@ struct MEBig {
 // Per-CTA working set of one step (always shared memory).  The fill candidates
 // of Algorithm 4 share storage with the affected-check list (not live then).
 struct MESmall {
-  int sel, est, best, cnl, cul, cbits, cnt, cntS, bits, touched, lbase, misc, total;
+  int sel, est, best, cnl, cul, cbits, cnt, cntS, bits, touched, misc, total;
 };
 
 __host__ __device__ inline MEBig me_big(int arith, int M, int N, int E) {
@@ -134,7 +134,7 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
   MESmall l;
   int o = 0;
   const int ncnl = n_p * (dvm > 1 ? dvm - 1 : 1);
-  l.sel = o; o = align16(o + n_p * 4);
+  l.sel = o; o = align16(o + 2 * n_p * 4);
   l.est = o; o = align16(o + n_p * 4);
   l.best = o; o = align16(o + n_p * 8);
   l.cnl = o; o = align16(o + (ncnl > kCap ? ncnl : kCap) * 8);
@@ -144,7 +144,6 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
   l.cntS = o; o = align16(o + n_g * 4);
   l.bits = o; o = align16(o + ((N + 31) / 32) * 4);
   l.touched = o; o = align16(o + ((N + 31) / 32) * 4);
-  l.lbase = o; o = align16(o + ((N + 31) / 32) * 4);
   l.misc = o; o = align16(o + 32 * 4);
   l.total = o;
   return l;
@@ -154,7 +153,7 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
 struct MEMisc {
   int unsat;
   int ncnu;  // affected (check, owner) pairs this step | distinct affected checks << 16
-  int nsel;  // selected VNs
+  int nsel[2];  // selected VNs of the two selection buffers (this step's, the next step's)
   int kstar, fill_g, need, top;
   int ncand;
   uint32_t thr, lo, hi;
@@ -177,7 +176,7 @@ struct MEState {
   Arr<int32_t> Lt;   // sum over the edges of each VN of L~^C, exact integer (see top)
   Arr<uint8_t> grp;
   Arr<uint32_t> par;
-  Arr<int32_t> sel;
+  Arr<int32_t> sel;    // two selection lists of n_p slots: this step's and the next step's
   Arr<int32_t> est;
   Arr<unsigned long long> best;
   Arr<int2> cnl;       // (check, owner k) of every affected check
@@ -188,7 +187,6 @@ struct MEState {
   Arr<int32_t> cntS;     // per-group count of the VNs excluded from Algorithm 4's search set
   Arr<uint32_t> bits;    // selection bitmap over VNs
   Arr<uint32_t> touched; // VNs whose D was rewritten in this step
-  Arr<int32_t> lbase;    // compaction: first selection slot of each bitmap word
   MEMisc* misc;
   const int16_t* tab;
   float fx, ifx;     // FP32 fixed point: 2^k and 2^-k
@@ -219,11 +217,13 @@ __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x &
 
 // Algorithm 4 over S = O_N minus nexcl excluded VNs (their bits are set and
 // s.cntS counts them per group): sets the bits of the selected VNs (at most
-// np).  Group sizes come from the maintained s.cnt.  All threads call it.
+// np) and appends them, in no particular order, to the selection list at
+// s.sel[sbase...] whose count is *nsel.  Group sizes come from the maintained
+// s.cnt.  All threads call it.
 template <int A, class X>
 __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, int nexcl, uint32_t step,
-                     uint64_t frame, uint64_t seed) {
-  const int tid = x.tid, nt = x.nt, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+                     uint64_t frame, uint64_t seed, int sbase, int* nsel) {
+  const int tid = x.tid, nt = x.nt, lane = tid & 31, warp = tid >> 5;
   MEMisc* ms = s.misc;
   if (warp == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S (one warp)
     // |G_i| over S = cnt[i] - cntS[i] (cntS counts the excluded VNs per group);
@@ -283,51 +283,98 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
   bool fill = need > 0;
   for (int iter = 0; iter < 64; ++iter) {
     const uint32_t thr = ms->thr;
-    for (int q0 = warp * 32; q0 < nq; q0 += nt) {  // warp-uniform trip count
-      const int q = q0 + lane;
-      unsigned fm = 0;
-      if (q < nq) {
-        // the quad's four group bytes compared at once (per-byte SIMD compares,
-        // then the byte masks packed to nibbles); VNs past N or already in
-        // the bitmap are not live; Q(k*) members go in with one atomic
-        const uint32_t g4 = *(const uint32_t*)&s.grp[4 * q];
-        const int sh = (q & 7) * 4;
-        const unsigned live = (N - 4 * q >= 4 ? 0xfu : ((1u << (N - 4 * q)) - 1u)) & ~((s.bits[q >> 3] >> sh) & 0xfu);
-        const uint32_t ge = __vcmpgeu4(g4, (uint32_t)top * 0x01010101u);
-        const uint32_t eq = __vcmpeq4(g4, (uint32_t)(fg & 0xff) * 0x01010101u);  // fg = -1: byte 255, no group
-        const unsigned gem = ((((ge >> 7) & 0x01010101u) * 0x01020408u) >> 24) & live;
-        fm = ((((eq >> 7) & 0x01010101u) * 0x01020408u) >> 24) & live;
-        if (iter == 0 && gem) atomicOr(&s.bits[q >> 3], gem << sh);
+    // two quads per lane (q0 + lane and q0 + 32 + lane): their Philox chains
+    // are independent and interleave; warp-uniform trip count
+    for (int q0 = warp * 64; q0 < nq; q0 += 2 * nt) {
+      unsigned fm[2] = {0u, 0u}, gem[2] = {0u, 0u};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + 32 * u + lane;
+        if (q < nq) {
+          // the quad's four group bytes compared at once (per-byte SIMD compares,
+          // then the byte masks packed to nibbles); VNs past N or already in
+          // the bitmap are not live; Q(k*) members go in with one atomic
+          const uint32_t g4 = *(const uint32_t*)&s.grp[4 * q];
+          const int sh = (q & 7) * 4;
+          const unsigned live = (N - 4 * q >= 4 ? 0xfu : ((1u << (N - 4 * q)) - 1u)) & ~((s.bits[q >> 3] >> sh) & 0xfu);
+          const uint32_t ge = __vcmpgeu4(g4, (uint32_t)top * 0x01010101u);
+          const uint32_t eq = __vcmpeq4(g4, (uint32_t)(fg & 0xff) * 0x01010101u);  // fg = -1: byte 255, no group
+          gem[u] = ((((ge >> 7) & 0x01010101u) * 0x01020408u) >> 24) & live;
+          fm[u] = ((((eq >> 7) & 0x01010101u) * 0x01020408u) >> 24) & live;
+          if (iter == 0 && gem[u]) atomicOr(&s.bits[q >> 3], gem[u] << sh);
+          if (iter != 0) gem[u] = 0u;
+        }
+      }
+      if (__any_sync(kFull, (gem[0] | gem[1]) != 0u)) {  // Q(k*) members of the warp's quads: one slot atomic
+        unsigned b[8];
+        int tot = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          b[i] = __ballot_sync(kFull, (gem[i >> 2] >> (i & 3)) & 1u);
+          tot += __popc(b[i]);
+        }
+        int base = 0;
+        if (lane == 0) base = atomicAdd(nsel, tot);
+        base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if ((gem[i >> 2] >> (i & 3)) & 1u)
+            s.sel[sbase + base + __popc(b[i] & lanemask_lt())] = 4 * (q0 + 32 * (i >> 2) + lane) + (i & 3);
+          base += __popc(b[i]);
+        }
       }
       if (!fill) continue;
-      uint32_t w[4] = {(uint32_t)q, step, (uint32_t)frame, (uint32_t)(frame >> 32)};
-      if (fm) philox4x32_10(w, seed);
+      uint32_t w[2][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const bool c = ((fm >> i) & 1u) && w[i] <= thr;
-        const unsigned bal = __ballot_sync(kFull, c);
-        if (!bal) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&ms->ncand, __popc(bal));
-        base = __shfl_sync(kFull, base, 0);
-        const int pos = base + __popc(bal & lanemask_lt());
-        if (c && pos < kCap) s.cand[pos] = ((unsigned long long)w[i] << 32) | (unsigned)(4 * q + i);
+      for (int u = 0; u < 2; ++u) {
+        w[u][0] = (uint32_t)(q0 + 32 * u + lane);
+        w[u][1] = step;
+        w[u][2] = (uint32_t)frame;
+        w[u][3] = (uint32_t)(frame >> 32);
+      }
+      if (fm[0] | fm[1]) {
+        philox4x32_10(w[0], seed);
+        philox4x32_10(w[1], seed);
+      }
+      // fill candidates (key <= thr) of both quads: one slot atomic
+      unsigned b[8];
+      int tot = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        b[i] = __ballot_sync(kFull, ((fm[i >> 2] >> (i & 3)) & 1u) && w[i >> 2][i & 3] <= thr);
+        tot += __popc(b[i]);
+      }
+      if (tot == 0) continue;
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&ms->ncand, tot);
+      base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int pos = base + __popc(b[i] & lanemask_lt());
+        if (((b[i] >> lane) & 1u) && pos < kCap)
+          s.cand[pos] = ((unsigned long long)w[i >> 2][i & 3] << 32) |
+                        (unsigned)(4 * (q0 + 32 * (i >> 2) + lane) + (i & 3));
+        base += __popc(b[i]);
       }
     }
     x.sync();
     if (!fill) break;
     const int nc = ms->ncand;
     if (nc >= need && nc <= kCap) {
-      // exact rank among the candidates ((key, n) is unique): a warp per
-      // candidate, its lanes splitting the comparisons
-      for (int c = warp; c < nc; c += nw) {
+      // exact rank among the candidates ((key, n) is unique): a thread per
+      // candidate counts the keys below its own (the lanes of a warp read the
+      // same key at a time: broadcast loads)
+      for (int c = tid; c < nc; c += nt) {
         const unsigned long long kc = s.cand[c];
         int rank = 0;
-        for (int c2 = lane; c2 < nc; c2 += 32) rank += s.cand[c2] < kc;
-        rank = __reduce_add_sync(kFull, rank);
-        if (lane == 0 && rank < need) {
+        int c2 = 0;
+        for (; c2 + 4 <= nc; c2 += 4)
+          rank += (s.cand[c2] < kc) + (s.cand[c2 + 1] < kc) + (s.cand[c2 + 2] < kc) + (s.cand[c2 + 3] < kc);
+        for (; c2 < nc; ++c2) rank += s.cand[c2] < kc;
+        if (rank < need) {
           const int n = (int)(kc & 0xffffffffull);
           atomicOr(&s.bits[n >> 5], 1u << (n & 31));
+          s.sel[sbase + atomicAdd(nsel, 1)] = n;
         }
       }
       x.sync();
@@ -348,45 +395,6 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
     }
     x.sync();
   }
-}
-
-// Compact the selection bitmap into s.sel (ascending), at most np entries; the
-// next step clears the bitmap.  Warp 0 splits the words into 32 ranges, scans
-// their counts and writes each word's first slot; then every thread expands
-// one word.
-template <int A, class X>
-__device__ void compact_selection(const X& x, int N, const MEState<A, X>& s, int np) {
-  const int lane = x.tid & 31, warp = x.tid >> 5, nw = x.nt >> 5;
-  const int words = (N + 31) / 32;
-  const int per = (words + 31) / 32;
-  if (warp == 0) {
-    const int w0 = lane * per, w1 = min(words, w0 + per);
-    int c = 0;
-    for (int w = w0; w < w1; ++w) c += __popc(s.bits[w]);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    int base = incl - c;
-    for (int w = w0; w < w1; ++w) {
-      s.lbase[w] = base;
-      base += __popc(s.bits[w]);
-    }
-    if (lane == 31) s.misc->nsel = min(incl, np);
-  }
-  x.sync();
-  for (int w = x.tid; w < words; w += x.nt) {
-    int pos = s.lbase[w];
-    uint32_t bw = s.bits[w];
-    while (bw != 0u && pos < np) {
-      const int bit = __ffs(bw) - 1;
-      bw &= bw - 1u;
-      s.sel[pos++] = w * 32 + bit;
-    }
-  }
-  x.sync();
 }
 
 // State views of a frame in one CTA: big arrays at `big` (shared memory or a
@@ -419,7 +427,6 @@ __device__ __forceinline__ MEState<A, CtaX> cta_state(const GraphDesc& gd, const
   s.cntS.p = (int32_t*)(small + ls.cntS);
   s.bits.p = (uint32_t*)(small + ls.bits);
   s.touched.p = (uint32_t*)(small + ls.touched);
-  s.lbase.p = (int32_t*)(small + ls.lbase);
   s.misc = (MEMisc*)(small + ls.misc);
   s.tab = tab_int;
   return s;
@@ -476,6 +483,8 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
   if (tid == 0) {
     ms->unsat = 0;
     ms->ncnu = 0;
+    ms->nsel[0] = 0;
+    ms->nsel[1] = 0;
   }
   if (x.sync_or(bad, &ms->orflag)) {
     for (int n = tid; n < N; n += nt) {
@@ -528,11 +537,10 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
 
   int64_t count = 0;
   uint32_t step = 0;
+  int cur = 0;  // selection buffer of this step (s.sel[cur * np ...], ms->nsel[cur])
   bool stop = a.check_interval > 0 && ms->unsat == 0;
-  if (!stop && io.max_updates > 0) {  // Alg. 5 line 4 / Alg. 6 line 4
-    alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed);
-    compact_selection<A, X>(x, N, s, np);
-  }
+  if (!stop && io.max_updates > 0)  // Alg. 5 line 4 / Alg. 6 line 4
+    alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed, 0, &ms->nsel[0]);
   // L~_j, D_j of VN j (j < 0: idle lane) unless already rewritten in this
   // step; group and group sizes follow.  All lanes of the warp call it.
   // With `want` the new D_j is also returned when another lane rewrites it (its
@@ -562,9 +570,17 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     return d;
   };
   while (!stop && count < io.max_updates) {
-    int nsel = ms->nsel;
+    // The selection list is in no particular order.  A VN's rank in ascending
+    // index order gives its trace position and, when the budget cuts the last
+    // step, whether it is kept (the lowest indices are); it is computed only then.
+    const int nsel = ms->nsel[cur];
     if (nsel <= 0) break;  // nothing selectable: the step would not advance
-    if ((int64_t)nsel > io.max_updates - count) nsel = (int)(io.max_updates - count);
+    const int64_t room = io.max_updates - count;
+    const bool trunc = (int64_t)nsel > room;
+    const bool ranked = trunc || io.trace != nullptr;
+    const int done = trunc ? (int)room : nsel;
+    const int so = cur * np, sn = (cur ^ 1) * np;
+    if (tid == 0) ms->nsel[cur ^ 1] = 0;  // read for the last time two steps ago
     // -- for each selected p (a team of Wv lanes, lane q on edge q of p):
     //    m*_p = argmax_i R_{i->p} on the pre-step state (the edges of p are
     //    disjoint from every other p's), commit L^C <- L~^C, L_p, syndrome,
@@ -576,12 +592,23 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     for (int k0 = warp * tpv; k0 < nsel; k0 += nw * tpv) {  // warp-uniform trip count
       const int k = k0 + vteam;
-      const bool act = k < nsel;
-      int p = 0, dv = 0, e = 0, m = 0;
+      bool act = k < nsel;
+      const int p = act ? s.sel[so + k] : 0;
+      int rank = k;
+      if (ranked) {  // team count of the selected VNs below p
+        int c = 0;
+        if (act)
+          for (int i = q; i < nsel; i += Wv) c += s.sel[so + i] < p;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          if (o < Wv) c += __shfl_xor_sync(kFull, c, o);
+        rank = c;
+        act = act && rank < done;
+      }
+      int dv = 0, e = 0, m = 0;
       uint32_t bk = 0, bi = 0xffffffffu;
       M_ pk = (M_)0, ck = (M_)0;
       if (act) {
-        p = s.sel[k];
         const typename G::V v = g.vn(p);
         dv = v.d;
         if (q < dv) {
@@ -626,7 +653,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         flip = (lold < (L_)0) != (lnew < (L_)0);
         s.L[p] = lnew;
         s.est[k] = (int)bi;
-        if (io.trace) io.trace[count + k] = (int)bi;
+        if (io.trace) io.trace[count + rank] = (int)bi;
       }
       flip = __shfl_sync(kFull, flip, vteam * Wv);
       int du = 0;
@@ -692,7 +719,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         }
         const D_ d = refresh_vn(j, true);
         unsigned long long key = 0ull;
-        if (j >= 0 && j != s.sel[k]) key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
+        if (j >= 0 && j != s.sel[so + k]) key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           if (o >= W) continue;
@@ -715,21 +742,20 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     // the selected VNs go to the last warps, which have the fewest pair teams
     for (int k0 = (nw - 1 - warp) * 32; k0 < nsel; k0 += nt) {
       const int k = k0 + lane;
-      refresh_vn(k < nsel ? s.sel[k] : -1, false);
+      refresh_vn(k < nsel ? s.sel[so + k] : -1, false);
     }
     x.sync();
     // the pair and check counts were read after the commit barrier; the next
     // commit phase, which counts again, starts after at least one more barrier
     if (tid == 0) ms->ncnu = 0;
-    count += nsel;
+    count += done;
     ++step;
-    if (a.check_interval > 0 && (count / a.check_interval) > ((count - nsel) / a.check_interval) &&
+    if (a.check_interval > 0 && (count / a.check_interval) > ((count - done) / a.check_interval) &&
         ms->unsat == 0)
       break;
     if (count >= io.max_updates) break;
     if constexpr (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
-      alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed);  // Alg. 5 line 4
-      compact_selection<A, X>(x, N, s, np);
+      alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed, sn, &ms->nsel[cur ^ 1]);  // Alg. 5 line 4
     } else {
       // -- P' = {argmax_{j in U(m*_p, p)} D_j} (degree-1 rule of Sec. 5.A:
       //    N(m*_p)\p), de-duplicated in the selection bitmap
@@ -738,7 +764,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         bool add = false;
         int j = 0;
         if (k < nsel) {
-          const int p = s.sel[k];
+          const int p = s.sel[so + k];
           const unsigned long long rg = s.best[k];
           const int first = (int)(rg >> 32), npair = (int)(rg & 0xffffffffull);
           unsigned long long bk = 0ull;
@@ -763,15 +789,21 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
           }
         }
         if (add) atomicAdd(&s.cntS[s.grp[j]], 1);  // per-group count of P' for Algorithm 4's top-up
+        const unsigned bal = __ballot_sync(kFull, add);  // P' joins the next selection list
+        int base = 0;
+        if (lane == 0 && bal != 0u) base = atomicAdd(&ms->nsel[cur ^ 1], __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (add) s.sel[sn + base + __popc(bal & lanemask_lt())] = j;
       }
       x.sync();
       // |P'| = the sum of its per-group counts (every warp, same value)
       int npp = 0;
       for (int i = lane; i < ng; i += 32) npp += s.cntS[i];
       npp = __reduce_add_sync(kFull, npp);
-      if (npp < np) alg4<A, X>(x, s, N, np - npp, ng, npp, step, frame, a.seed);  // lines 11-13
-      compact_selection<A, X>(x, N, s, np);
+      if (npp < np)  // lines 11-13
+        alg4<A, X>(x, s, N, np - npp, ng, npp, step, frame, a.seed, sn, &ms->nsel[cur ^ 1]);
     }
+    cur ^= 1;
   }
 
   for (int n = tid; n < N; n += nt) {
@@ -914,9 +946,8 @@ __device__ __forceinline__ MEState<A, ClusterX> cluster_state(const DecodeArgs& 
   LDPC_DARR(cntS, int32_t, 15);
   LDPC_DARR(bits, uint32_t, 16);
   LDPC_DARR(touched, uint32_t, 17);
-  LDPC_DARR(lbase, int32_t, 18);
 #undef LDPC_DARR
-  s.misc = cg::this_cluster().map_shared_rank((MEMisc*)(base + c.off[19]), (unsigned)c.rank0[19]);
+  s.misc = cg::this_cluster().map_shared_rank((MEMisc*)(base + c.off[18]), (unsigned)c.rank0[18]);
   s.tab = tab_int;
   return s;
 }
@@ -932,8 +963,8 @@ __global__ void __launch_bounds__(TPB, 1) me_cluster_kernel(const DecodeArgs a) 
     for (int i = threadIdx.x; i < 256; i += blockDim.x) tab_int[i] = a.ci_table[i];
   const cg::cluster_group cl = cg::this_cluster();
   unsigned char* base = smem_raw + a.graph_smem;
-  if (cl.block_rank() == (unsigned)a.cl.rank0[19] && threadIdx.x == 0)
-    ((MEMisc*)(base + a.cl.off[19]))->orflag = 0;
+  if (cl.block_rank() == (unsigned)a.cl.rank0[18] && threadIdx.x == 0)
+    ((MEMisc*)(base + a.cl.off[18]))->orflag = 0;
   const ClusterX x;
   x.sync();  // every CTA of the cluster runs before any distributed address is formed
   MEState<A, ClusterX> s = cluster_state<A>(a, base, tab_int);
@@ -1053,9 +1084,9 @@ bool me_cluster_plan(int arith, const GraphDesc& g, int n_p, int n_g, int cs, in
   const int64_t Mw = (g.M + 31) / 32, Nw = (g.N + 31) / 32;
   // elements and element sizes in array order
   const int64_t n[kClusterArrays] = {g.E, g.E, g.N, g.N, g.N, g.N, g.N, Mw,
-                                     n_p, n_p, n_p, std::max<int64_t>(ncnl, kCap), ncnl, Mw, n_g, n_g,
-                                     Nw, Nw, Nw, 1};
-  const int sz[kClusterArrays] = {msg, msg, llr, llr, dv, 4, 1, 4, 4, 4, 8, 8, 4, 4, 4, 4, 4, 4, 4,
+                                     2 * (int64_t)n_p, n_p, n_p, std::max<int64_t>(ncnl, kCap), ncnl, Mw, n_g, n_g,
+                                     Nw, Nw, 1};
+  const int sz[kClusterArrays] = {msg, msg, llr, llr, dv, 4, 1, 4, 4, 4, 8, 8, 4, 4, 4, 4, 4, 4,
                                   (int)sizeof(MEMisc)};
   ClusterPlan p;
   std::memset(&p, 0, sizeof(p));
