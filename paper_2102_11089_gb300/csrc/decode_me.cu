@@ -154,10 +154,9 @@ struct MEMisc {
   int unsat;
   int ncnu;  // affected (check, owner) pairs this step | distinct affected checks << 16
   int nsel[2];  // selected VNs of the two selection buffers (this step's, the next step's)
-  int kstar, fill_g, need, top;
-  int ncand;
+  int ncand;  // fill candidates gathered (reset at every step start)
   uint32_t thr, lo, hi;
-  int done, hi_set;
+  int hi_set;
   int orflag;  // cluster form: OR of the bad-input flags
 };
 
@@ -225,64 +224,59 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
                      uint64_t frame, uint64_t seed, int sbase, int* nsel) {
   const int tid = x.tid, nt = x.nt, lane = tid & 31, warp = tid >> 5;
   MEMisc* ms = s.misc;
-  if (warp == 0) {  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S (one warp)
-    // |G_i| over S = cnt[i] - cntS[i] (cntS counts the excluded VNs per group);
-    // lane l of chunk b looks at group ng - 1 - (b + l), i.e. k = b + l + 1
-    const int sz = N - nexcl;
-    int kstar = 0, q = 0;
-    if (sz <= np) {
-      kstar = ng;
-      q = sz;
-    } else {
-      for (int b0 = 0; b0 < ng - 1; b0 += 32) {
-        const int i = b0 + lane;
-        const int c = i < ng - 1 ? s.cnt[ng - 1 - i] - s.cntS[ng - 1 - i] : np + 1;  // > np, no overflow
-        int pre = c;
+  // line 3: k* = max{k : |Q(k)| <= N_P} on the counts of S, by every warp from
+  // the maintained counts (the same values everywhere, no barrier); warp 0
+  // stores the state of the threshold search.  |G_i| over S = cnt[i] - cntS[i]
+  // (cntS counts the excluded VNs per group); lane l of chunk b looks at group
+  // ng - 1 - (b + l), i.e. k = b + l + 1
+  const int sz = N - nexcl;
+  int kstar = 0, q = 0;
+  if (sz <= np) {
+    kstar = ng;
+    q = sz;
+  } else {
+    for (int b0 = 0; b0 < ng - 1; b0 += 32) {
+      const int i = b0 + lane;
+      const int c = i < ng - 1 ? s.cnt[ng - 1 - i] - s.cntS[ng - 1 - i] : np + 1;  // > np, no overflow
+      int pre = c;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, pre, o);
-          if (lane >= o) pre += y;
-        }
-        const unsigned ok = __ballot_sync(kFull, q + pre <= np);  // a prefix of the lanes
-        const int nok = __popc(ok);
-        kstar += nok;
-        q += nok > 0 ? __shfl_sync(kFull, pre, nok - 1) : 0;
-        if (nok < 32) break;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += y;
       }
-    }
-    if (lane == 0) {
-      const int need = kstar < ng ? np - q : 0;
-      ms->kstar = kstar;
-      ms->top = ng - kstar;
-      ms->need = need;
-      ms->fill_g = ng - kstar - 1;
-      ms->thr = 0xffffffffu;
-      if (need > 0) {
-        // first threshold: need + 3 sqrt(need) + 8 expected members at or below
-        // it, short of `need` with probability < 1e-3 (the selection does not
-        // depend on it)
-        const int fg = ng - kstar - 1;
-        const int members = s.cnt[fg] - s.cntS[fg];
-        const float want = (float)need + 3.0f * sqrtf((float)need) + 8.0f;
-        if ((float)members > want) {
-          const float t = want / (float)members * 4294967296.0f;
-          ms->thr = t >= 4294967040.0f ? 0xffffffffu : (uint32_t)t;
-        }
-      }
-      ms->lo = 0;
-      ms->hi = 0xffffffffu;
-      ms->hi_set = 0;
-      ms->ncand = 0;
+      const unsigned ok = __ballot_sync(kFull, q + pre <= np);  // a prefix of the lanes
+      const int nok = __popc(ok);
+      kstar += nok;
+      q += nok > 0 ? __shfl_sync(kFull, pre, nok - 1) : 0;
+      if (nok < 32) break;
     }
   }
-  x.sync();
-  const int top = ms->top, fg = ms->fill_g, need = ms->need;
+  const int need = kstar < ng ? np - q : 0;
+  const int top = ng - kstar, fg = ng - kstar - 1;
+  uint32_t thr0 = 0xffffffffu;
+  if (need > 0) {
+    // first threshold: need + 3 sqrt(need) + 8 expected members at or below
+    // it, short of `need` with probability < 1e-3 (the selection does not
+    // depend on it)
+    const int members = s.cnt[fg] - s.cntS[fg];
+    const float want = (float)need + 3.0f * sqrtf((float)need) + 8.0f;
+    if ((float)members > want) {
+      const float t = want / (float)members * 4294967296.0f;
+      thr0 = t >= 4294967040.0f ? 0xffffffffu : (uint32_t)t;
+    }
+  }
+  if (tid == 0) {  // read only after the pass's barrier
+    ms->thr = thr0;
+    ms->lo = 0;
+    ms->hi = 0xffffffffu;
+    ms->hi_set = 0;
+  }
   const int nq = (N + 3) / 4;
   // one pass over VN quads: line 3 selects Q(k*); lines 4-6 gather fill candidates
   // (key = word i of the Philox block of quad q)
   bool fill = need > 0;
   for (int iter = 0; iter < 64; ++iter) {
-    const uint32_t thr = ms->thr;
+    const uint32_t thr = iter == 0 ? thr0 : ms->thr;
     // two quads per lane (q0 + lane and q0 + 32 + lane): their Philox chains
     // are independent and interleave; warp-uniform trip count
     for (int q0 = warp * 64; q0 < nq; q0 += 2 * nt) {
@@ -485,6 +479,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     ms->ncnu = 0;
     ms->nsel[0] = 0;
     ms->nsel[1] = 0;
+    ms->ncand = 0;
   }
   if (x.sync_or(bad, &ms->orflag)) {
     for (int n = tid; n < N; n += nt) {
@@ -580,7 +575,10 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     const bool ranked = trunc || io.trace != nullptr;
     const int done = trunc ? (int)room : nsel;
     const int so = cur * np, sn = (cur ^ 1) * np;
-    if (tid == 0) ms->nsel[cur ^ 1] = 0;  // read for the last time two steps ago
+    if (tid == 0) {
+      ms->nsel[cur ^ 1] = 0;  // read for the last time two steps ago
+      ms->ncand = 0;          // read for the last time before the previous step's last barrier
+    }
     // -- for each selected p (a team of Wv lanes, lane q on edge q of p):
     //    m*_p = argmax_i R_{i->p} on the pre-step state (the edges of p are
     //    disjoint from every other p's), commit L^C <- L~^C, L_p, syndrome,
@@ -589,7 +587,6 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
       s.bits[w] = 0u;
       s.touched[w] = 0u;
     }
-    for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     for (int k0 = warp * tpv; k0 < nsel; k0 += nw * tpv) {  // warp-uniform trip count
       const int k = k0 + vteam;
       bool act = k < nsel;
@@ -687,6 +684,10 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     }
     x.sync();
     const int ncn = ms->ncnu & 0xffff, ncu = ms->ncnu >> 16;
+    // per-group counts of P': every warp summed them after the previous P'
+    // barrier, and a warp that skipped the top-up met no barrier since; all
+    // have passed the commit barrier now
+    for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     // -- precomputed C2V of every affected check (once per check); the L~ sums
     //    of its variables follow by exact deltas
     for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {

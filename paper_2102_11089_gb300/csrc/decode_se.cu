@@ -37,8 +37,57 @@ struct SEState {
   M_* Rmax;
   int32_t* Ridx;
   uint32_t* par;
+  uint32_t* Dblk;    // largest key of D per block of 32 VNs (CIRBP)
+  uint32_t* Ddirty;  // blocks whose largest D may have dropped
+  uint32_t* Rblk;    // largest per-check residual key per block of 32 checks (RBP, CIRBP)
+  uint32_t* Rdirty;
   int16_t* tab;
 };
+
+// Upper level of the global argmaxes: blk[b] is the largest key of block b (32
+// entries).  A key that grows raises its block's entry at once; a key that
+// drops from a block's largest value marks the block dirty, and the block is
+// recomputed before the next search (blk_fix).  The entry thus always equals
+// the block's largest key when it is read.
+__device__ __forceinline__ void blk_note(uint32_t* blk, uint32_t* dirty, int i, uint32_t kold, uint32_t knew) {
+  const int b = i >> 5;
+  if (knew > kold) atomicMax(&blk[b], knew);
+  else if (knew < kold && kold == blk[b]) atomicOr(&dirty[b >> 5], 1u << (b & 31));
+}
+
+// recompute the dirty blocks (whole warp); key(i) is entry i's key, 0 past n
+template <class K>
+__device__ __forceinline__ void blk_fix(uint32_t* blk, uint32_t* dirty, int n, const K& key) {
+  const int lane = threadIdx.x & 31, nb = (n + 31) >> 5;
+  __syncwarp();
+  for (int w = 0; w < ((nb + 31) >> 5); ++w) {
+    uint32_t dm = dirty[w];
+    if (dm == 0u) continue;
+    __syncwarp();
+    if (lane == 0) dirty[w] = 0u;
+    while (dm != 0u) {
+      const int b = w * 32 + __ffs(dm) - 1;
+      dm &= dm - 1u;
+      const int i = b * 32 + lane;
+      const uint32_t mx = __reduce_max_sync(kFull, i < n ? key(i) : 0u);
+      if (lane == 0) blk[b] = mx;
+    }
+  }
+  __syncwarp();
+}
+
+// every block from scratch (whole warp)
+template <class K>
+__device__ __forceinline__ void blk_build(uint32_t* blk, uint32_t* dirty, int n, const K& key) {
+  const int lane = threadIdx.x & 31, nb = (n + 31) >> 5;
+  for (int b = 0; b < nb; ++b) {
+    const int i = b * 32 + lane;
+    const uint32_t mx = __reduce_max_sync(kFull, i < n ? key(i) : 0u);
+    if (lane == 0) blk[b] = mx;
+  }
+  for (int w = lane; w < ((nb + 31) >> 5); w += 32) dirty[w] = 0u;
+  __syncwarp();
+}
 
 __device__ __forceinline__ float ci_val(const SEState<kFP32>&, float a, float b) { return ci_fp(a, b); }
 __device__ __forceinline__ uint16_t ci_val(const SEState<kINT6>& s, int a, int b) {
@@ -72,6 +121,27 @@ __device__ __forceinline__ int global_argmax_D(int N, const SEState<A>& s, uint3
   return (int)warp_argmax(bk, bi, key);
 }
 
+// the same through the block maxima: the first block holding the largest key,
+// then the lowest index with that key in it
+template <int A>
+__device__ __forceinline__ int global_argmax_D_blk(int N, const SEState<A>& s, uint32_t& key) {
+  const int lane = threadIdx.x & 31, nb = (N + 31) >> 5;
+  blk_fix(s.Dblk, s.Ddirty, N, [&](int i) { return mkey(s.D[i]); });
+  uint32_t bk = 0, bi = 0xffffffffu;
+  for (int b = lane; b < nb; b += 32) {
+    const uint32_t k = s.Dblk[b];
+    if (k > bk || bi == 0xffffffffu) {
+      bk = k;
+      bi = (uint32_t)b;
+    }
+  }
+  const int B = (int)warp_argmax(bk, bi, key);
+  const int n = B * 32 + lane;
+  const bool hit = n < N && mkey(s.D[n]) == key;
+  const uint32_t r = __reduce_min_sync(kFull, hit ? (uint32_t)n : 0xffffffffu);
+  return r != 0xffffffffu ? (int)r : global_argmax_D<A>(N, s, key);  // (the block entries are exact)
+}
+
 // argmax over the residual of every edge, eq. (5), via the per-check maxima
 template <int A>
 __device__ __forceinline__ int global_argmax_R(int M, const SEState<A>& s) {
@@ -87,9 +157,34 @@ __device__ __forceinline__ int global_argmax_R(int M, const SEState<A>& s) {
   return (int)warp_argmax(bk, bi, key);
 }
 
-// per-check largest residual (value, lowest edge id), one lane
+// the same through the block maxima of the per-check residual maxima (edge ids
+// grow with the check index, so the lowest check holding the largest key has
+// the lowest edge id among them)
+template <int A>
+__device__ __forceinline__ int global_argmax_R_blk(int M, const SEState<A>& s) {
+  using M_ = typename Arith<A>::msg;
+  const int lane = threadIdx.x & 31, mb = (M + 31) >> 5;
+  blk_fix(s.Rblk, s.Rdirty, M, [&](int m) { return rkey(s.Rmax[m], (M_)0); });
+  uint32_t bk = 0, bi = 0xffffffffu;
+  for (int b = lane; b < mb; b += 32) {
+    const uint32_t k = s.Rblk[b];
+    if (k > bk || bi == 0xffffffffu) {
+      bk = k;
+      bi = (uint32_t)b;
+    }
+  }
+  uint32_t key;
+  const int B = (int)warp_argmax(bk, bi, key);
+  const int m = B * 32 + lane;
+  const bool hit = m < M && rkey(s.Rmax[m], (M_)0) == key;
+  const uint32_t mm = __reduce_min_sync(kFull, hit ? (uint32_t)m : 0xffffffffu);
+  return mm != 0xffffffffu ? s.Ridx[mm] : global_argmax_R<A>(M, s);  // (the block entries are exact)
+}
+
+// per-check largest residual (value, lowest edge id), one lane; with `blk` the
+// block maxima follow
 template <int A, class G>
-__device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, int m) {
+__device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, int m, bool blk = false) {
   const typename G::C cc = g.cn(m);
   uint32_t bk = 0, bi = (uint32_t)cc.b;
   for (int e = cc.b; e < cc.b + cc.d; ++e) {
@@ -100,9 +195,11 @@ __device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, in
     }
   }
   using M_ = typename Arith<A>::msg;
+  const uint32_t kold = blk ? rkey(s.Rmax[m], (M_)0) : 0u;
   if (A == kFP32) s.Rmax[m] = (M_)__uint_as_float(bk);
   else s.Rmax[m] = (M_)bk;
   s.Ridx[m] = (int32_t)bi;
+  if (blk) blk_note(s.Rblk, s.Rdirty, m, kold, bk);
 }
 
 // Decode one frame of code `gd` with its state at `base` (shared or global memory).
@@ -113,6 +210,8 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   constexpr bool kNeedR = SCHED != kLMD;
+  constexpr bool kDblk = SCHED == kCIRBP;                     // global argmax of D every update
+  constexpr bool kRblk = SCHED == kCIRBP || SCHED == kRBP;    // global argmax of the residuals
   const int lane = threadIdx.x & 31;
   const int N = gd.N, E = gd.E, M = gd.M;
   const SELayout ly = se_layout(A, M, N, E, kNeedR);
@@ -125,6 +224,10 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   s.Rmax = (M_*)(base + ly.Rmax);
   s.Ridx = (int32_t*)(base + ly.Ridx);
   s.par = (uint32_t*)(base + ly.par);
+  s.Dblk = (uint32_t*)(base + ly.Dblk);
+  s.Ddirty = (uint32_t*)(base + ly.Ddirty);
+  s.Rblk = (uint32_t*)(base + ly.Rblk);
+  s.Rdirty = (uint32_t*)(base + ly.Rdirty);
   s.tab = (int16_t*)(base + ly.tab);
   const float clip = a.llr_clip;
   const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
@@ -190,6 +293,18 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   if (kNeedR)
     for (int m = lane; m < M; m += 32) refresh_rmax<A, G>(g, s, m);
   __syncwarp();
+  if (kDblk) blk_build(s.Dblk, s.Ddirty, N, [&](int i) { return mkey(s.D[i]); });
+  if (kRblk) blk_build(s.Rblk, s.Rdirty, M, [&](int m) { return rkey(s.Rmax[m], (M_)0); });
+  // D_j <- d, with the block maxima of CIRBP's global argmax
+  auto set_D = [&](int j, D_ d) {
+    if (kDblk) {
+      const uint32_t ko = mkey(s.D[j]);
+      s.D[j] = d;
+      blk_note(s.Dblk, s.Ddirty, j, ko, mkey(d));
+    } else {
+      s.D[j] = d;
+    }
+  };
 
   // ---- schedule loop
   constexpr bool kLMDR = SCHED == kLMDRBP || SCHED == kSLMDRBP;
@@ -205,7 +320,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     // -- selection
     int eglob = -1;  // RBP / CIRBP fallback: the global residual argmax fixes e*
     if (SCHED == kRBP) {
-      eglob = global_argmax_R<A>(M, s);
+      eglob = global_argmax_R_blk<A>(M, s);
       nstar = g.evn(eglob);
     } else if (kLMDR) {
       if (enext < 0) {  // Alg. 2 line 3, and an empty candidate set
@@ -217,10 +332,10 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
       }
     } else if (SCHED == kCIRBP) {
       uint32_t dkey;
-      nstar = global_argmax_D<A>(N, s, dkey);
+      nstar = global_argmax_D_blk<A>(N, s, dkey);
       const bool fallback = (A == kFP32) ? (__uint_as_float(dkey) < a.gamma_f) : ((int)dkey < a.gamma_i);
       if (fallback) {  // Alg. 1 line 6
-        eglob = global_argmax_R<A>(M, s);
+        eglob = global_argmax_R_blk<A>(M, s);
         nstar = g.evn(eglob);
         ++nfall;
       }
@@ -264,7 +379,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     if (lane == kstar) s.C[estar] = my_p;
     if (lane == 0) {
       s.L[nstar] = Lnew;
-      s.D[nstar] = ci_val(s, Lnew, Ltn);  // reading: D of n* follows L_{n*}
+      set_D(nstar, ci_val(s, Lnew, Ltn));  // reading: D of n* follows L_{n*}
     }
     if ((Lold < (L_)0) != (Lnew < (L_)0)) {  // tentative decision flipped
       int delta = 0;
@@ -298,7 +413,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
       __syncwarp();
       if (mine) {
         const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
-        s.D[j] = d;
+        set_D(j, d);
         am_update(ck, cidx, mkey(d), (uint32_t)j);
       }
     } else {
@@ -325,12 +440,12 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
         const int j = g.cvn(cc, r);
         if (j == nstar) continue;
         const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
-        s.D[j] = d;
+        set_D(j, d);
         am_update(ck, cidx, mkey(d), (uint32_t)j);
       }
     }
     __syncwarp();
-    if (kNeedR && lane < dv) refresh_rmax<A, G>(g, s, my_m);
+    if (kNeedR && lane < dv) refresh_rmax<A, G>(g, s, my_m, kRblk);
     __syncwarp();
 
     ++count;

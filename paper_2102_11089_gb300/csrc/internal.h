@@ -46,7 +46,7 @@ struct GraphDesc {
 // in the shared memory of the CTAs of a cluster.  Element i of array k is in
 // rank rank0[k] + (i >> shift[k]), at byte off[k] + (i & (2^shift[k] - 1)) *
 // element size from the start of that CTA's state area.
-constexpr int kClusterArrays = 20;  // C P lam L D Lt grp par | sel est best cnl cul cbits cnt cntS bits touched lbase misc
+constexpr int kClusterArrays = 19;  // C P lam L D Lt grp par | sel est best cnl cul cbits cnt cntS bits touched misc
 struct ClusterPlan {
   int32_t cs;     // CTAs per cluster (0: not the cluster form)
   int32_t bytes;  // state bytes per CTA
@@ -152,9 +152,12 @@ inline __host__ __device__ int graph_smem_bytes(const GraphDesc& d) {
   return d.tab_in_smem ? align16(d.tab_words * 4) : 0;
 }
 
-// Per-frame state layout of the single-edge (warp per frame) decoder.
+// Per-frame state layout of the single-edge (warp per frame) decoder.  Dblk /
+// Rblk: the largest metric key of each block of 32 VNs / 32 checks (the upper
+// level of the global argmax of CIRBP and RBP), with dirty bits of blocks
+// whose maximum may have dropped.
 struct SELayout {
-  int C, P, lam, L, D, Rmax, Ridx, par, tab, total;
+  int C, P, lam, L, D, Rmax, Ridx, par, Dblk, Ddirty, Rblk, Rdirty, tab, total;
 };
 
 inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bool need_r) {
@@ -171,6 +174,11 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bo
   l.Rmax = o; o = align16(o + (need_r ? M * msg : 0));
   l.Ridx = o; o = align16(o + (need_r ? M * 4 : 0));
   l.par = o; o = align16(o + ((M + 31) / 32) * 4);
+  const int nb = (N + 31) / 32, mb = (M + 31) / 32;
+  l.Dblk = o; o = align16(o + nb * 4);
+  l.Ddirty = o; o = align16(o + ((nb + 31) / 32) * 4);
+  l.Rblk = o; o = align16(o + (need_r ? mb * 4 : 0));
+  l.Rdirty = o; o = align16(o + (need_r ? ((mb + 31) / 32) * 4 : 0));
   l.tab = o; o = align16(o + (arith == kINT6 ? 256 * 2 : 0));
   l.total = o;
   return l;
