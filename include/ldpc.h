@@ -159,6 +159,19 @@ ldpc_status_t ldpc_code_create(const int32_t *check_idx, const int32_t *var_idx,
                                int32_t n_checks, int32_t n_vars, const uint8_t *punctured,
                                int32_t k_info, ldpc_code_t **out);
 
+/* Seeded random (dv, dc)-regular code (the regular Tanner graphs of Sec. 2.A;
+ * the (3,6) workload of the small experiments).  dv sockets per variable and dc
+ * per check; the check sockets are shuffled (Fisher-Yates on SplitMix64 with the
+ * given seed) and matched to the variable sockets in order; double edges, and
+ * with girth6 != 0 the 4-cycles, are removed by seeded swaps of the check
+ * endpoints of two edges (degrees are kept).  Deterministic for a seed.
+ * n_checks = n dv / dc; k_info <= 0 takes the design value n - n_checks.
+ * Host-side only.  Errors: INVALID_ARG (n dv not a multiple of dc, degrees
+ * outside 1..32 or larger than the other side, n > 2^22), UNSUPPORTED (the
+ * double edges / 4-cycles could not be removed in 200,000 trials), NOMEM. */
+ldpc_status_t ldpc_code_build_regular(int32_t n, int32_t dv, int32_t dc, uint64_t seed, int32_t girth6,
+                                      int32_t k_info, ldpc_code_t **out);
+
 /* Build a quasi-cyclic code by circulant lifting of a protograph.
  * base       : host int32[rows * cols], row-major; -1 = zero block, s >= 0 =
  *              Z x Z circulant whose row z has its one in column (z + s) mod Z,

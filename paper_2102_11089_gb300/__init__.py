@@ -86,6 +86,7 @@ def _load():
             ("ldpc_default_params", [P]),
             ("ldpc_code_create", [P, P, I64, I32, I32, P, I32, P]),
             ("ldpc_code_build_qc", [P, I32, I32, I32, P, I32, P]),
+            ("ldpc_code_build_regular", [I32, I32, I32, U64, I32, I32, P]),
             ("ldpc_code_destroy", [P]),
             ("ldpc_code_info", [P, P]),
             ("ldpc_code_edges", [P, P, P]),
@@ -150,6 +151,14 @@ class Code:
         out = ctypes.c_void_p()
         _check(_load().ldpc_code_build_qc(_np_ptr(b), rows, cols, Z, _np_ptr(pc), k_info,
                                           ctypes.byref(out)))
+        return cls(out)
+
+    @classmethod
+    def regular(cls, n: int, dv: int, dc: int, seed: int, *, girth6: bool = True, k_info: int = 0) -> "Code":
+        """ldpc_code_build_regular: seeded (dv, dc)-regular code, double edges
+        (and 4-cycles) removed."""
+        out = ctypes.c_void_p()
+        _check(_load().ldpc_code_build_regular(n, dv, dc, seed, int(girth6), k_info, ctypes.byref(out)))
         return cls(out)
 
     @property

@@ -67,19 +67,23 @@ __device__ __forceinline__ float combine_fp(float sum_phi, unsigned neg, float c
 
 __device__ __forceinline__ int8_t encode_int(int v) { return (int8_t)max(-31, min(31, v)); }
 
-// |p0(a) - p0(b)| of eq. (8), p0(L) = e^L/(1+e^L), without the cancellation of
-// 1 - 1: with x = |a|, y = |b|, ex = e^-x, ey = e^-y,
-//   equal signs    : e^-min(x,y) (1 - e^-|x-y|) / ((1+ex)(1+ey))
-//   opposite signs : ((1-ex)/(1+ex) + (1-ey)/(1+ey)) / 2  (= (tanh(x/2)+tanh(y/2))/2)
-// Both are evaluated and one selected (no divergent branch in a lane team).
+// |p0(a) - p0(b)| of eq. (8), p0(L) = e^L/(1+e^L) = (1 + tanh(L/2))/2, without
+// the cancellation of 1 - 1: with x = |a|, y = |b|, ex = e^-x, ey = e^-y and
+// tanh(x/2) = (1 - ex)/(1 + ex), both sign cases share one denominator:
+//   opposite signs : (tanh(x/2) + tanh(y/2)) / 2 = (1 - e^-(x+y)) / ((1+ex)(1+ey))
+//   equal signs    : |tanh(x/2) - tanh(y/2)| / 2 = |ex - ey| / ((1+ex)(1+ey))
+//                    with |ex - ey| = e^-min(x,y) (1 - e^-|x-y|)
+// 1 - e^-u comes from its Taylor polynomial for u < 1/4 (no cancellation),
+// else from the exponentials at hand.  Both numerators are evaluated and one
+// selected (no divergent branch in a lane team).
 __device__ __forceinline__ float ci_fp(float a, float b) {
   const float x = fabsf(a), y = fabsf(b);
   const float ex = expf(-x), ey = expf(-y);
-  const float opposite = 0.5f * (__fdividef(1.0f - ex, 1.0f + ex) + __fdividef(1.0f - ey, 1.0f + ey));
-  const float d = fabsf(x - y);
-  const float omd = d < 0.25f ? one_minus_exp_small(d) : 1.0f - expf(-d);
-  const float equal = __fdividef(fmaxf(ex, ey) * omd, (1.0f + ex) * (1.0f + ey));
-  return (a >= 0.0f) != (b >= 0.0f) ? opposite : equal;
+  const float sum = x + y, d = fabsf(x - y);
+  const float opposite = sum < 0.25f ? one_minus_exp_small(sum) : 1.0f - ex * ey;
+  const float hi = fmaxf(ex, ey);
+  const float equal = d < 0.25f ? hi * one_minus_exp_small(d) : hi - fminf(ex, ey);
+  return __fdividef((a >= 0.0f) != (b >= 0.0f) ? opposite : equal, (1.0f + ex) * (1.0f + ey));
 }
 
 // Integer CI: |T[c(a)] - T[c(b)]| with c = clamp to [-127, 127].

@@ -236,3 +236,30 @@ def test_encode_plan_needs_no_gpu(lib):
     base = np.zeros((3, 6), np.int32)  # all-ones protograph: no dual-diagonal core
     qc = L.Code.from_protograph(base, 4, 12)
     assert lib.ldpc_encode(qc._h, null, 0, null, null) == -5
+
+
+@pytest.mark.parametrize("n,dv,dc", [(96, 3, 6), (2304, 3, 6), (1000, 4, 8), (99, 3, 9)])
+def test_build_regular_code_is_regular_with_girth_six(lib, n, dv, dc):
+    # ldpc_code_build_regular: exact degrees, no double edge, no 4-cycle (two
+    # checks share at most one variable), deterministic for a seed
+    code = L.Code.regular(n, dv, dc, 7)
+    assert (code.N, code.M, code.E, code.K) == (n, n * dv // dc, n * dv, n - n * dv // dc)
+    c, v = code.edges()
+    H = np.zeros((code.M, code.N), np.int64)
+    np.add.at(H, (c, v), 1)
+    assert H.max() == 1
+    assert set(H.sum(0)) == {dv} and set(H.sum(1)) == {dc}
+    ov = H @ H.T
+    np.fill_diagonal(ov, 0)
+    assert ov.max() <= 1
+    c2, v2 = L.Code.regular(n, dv, dc, 7).edges()
+    assert np.array_equal(c, c2) and np.array_equal(v, v2)
+    c3, v3 = L.Code.regular(n, dv, dc, 8).edges()
+    assert not (np.array_equal(c, c3) and np.array_equal(v, v3))
+
+
+def test_build_regular_rejects_bad_shapes(lib):
+    for args in [(97, 3, 6), (96, 0, 6), (96, 3, 1), (96, 3, 40), (4, 3, 6)]:
+        with pytest.raises(L.LdpcError) as e:
+            L.Code.regular(*args, 1)
+        assert e.value.name == "LDPC_ERR_INVALID_ARG"
