@@ -68,6 +68,8 @@ typedef int32_t ldpc_status_t;
 #define LDPC_FORM_GLOBAL 2 /* frame state in device global memory (large codes)   */
 #define LDPC_FORM_CLUSTER 3 /* multi-edge: frame state spread over the shared memory
                              of a thread-block cluster (large codes)          */
+#define LDPC_FORM_SPLIT 4   /* single-edge: VN- and check-sized arrays in shared
+                             memory, the edge arrays in global memory (L2)    */
 
 /* per-frame flag bits written to `converged` */
 #define LDPC_FRAME_CONVERGED 1u /* final hard decision satisfies every check      */

@@ -17,14 +17,14 @@ __all__ = [
     "LdpcError", "Code", "DecodeParams", "decode", "decode_noalloc", "decode_queue", "make_items", "awgn_llr",
     "sync", "library_path", "QUEUE_STATIC", "QUEUE_PERSISTENT",
     "SCHEDULES", "FLOODING", "RBP", "CIRBP", "LMD_CIRBP", "ME_CIRBP", "ME_LMD_CIRBP",
-    "FP32_SUMPRODUCT", "INT6_MINSUM", "FORM_AUTO", "FORM_SMEM", "FORM_GLOBAL",
+    "FP32_SUMPRODUCT", "INT6_MINSUM", "FORM_AUTO", "FORM_SMEM", "FORM_GLOBAL", "FORM_CLUSTER", "FORM_SPLIT",
 ]
 
 FLOODING, RBP, CIRBP, LMD_CIRBP, ME_CIRBP, ME_LMD_CIRBP, LMDRBP, SLMDRBP = range(8)
 SCHEDULES = {"flooding": FLOODING, "rbp": RBP, "cirbp": CIRBP, "lmd-cirbp": LMD_CIRBP,
              "me-cirbp": ME_CIRBP, "me-lmd-cirbp": ME_LMD_CIRBP, "lmdrbp": LMDRBP, "slmdrbp": SLMDRBP}
 FP32_SUMPRODUCT, INT6_MINSUM = 0, 1
-FORM_AUTO, FORM_SMEM, FORM_GLOBAL, FORM_CLUSTER = 0, 1, 2, 3
+FORM_AUTO, FORM_SMEM, FORM_GLOBAL, FORM_CLUSTER, FORM_SPLIT = 0, 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "_lib", "libldpc_gb300.so")

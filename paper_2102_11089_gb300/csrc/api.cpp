@@ -548,10 +548,12 @@ ldpc_status_t ldpc_decode_ex(const ldpc_code_t* code, const void* llr, int64_t b
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (ldpc::is_multi_edge(p->schedule) && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 1024))
     return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 1024 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0x1ff) != 0 || (p->tune & 3) == 3)
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_SPLIT || (p->tune & ~0x1ff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (p->form == LDPC_FORM_CLUSTER && !ldpc::is_multi_edge(p->schedule))
     return fail(LDPC_ERR_UNSUPPORTED, "the cluster form runs the multi-edge schedules");
+  if (p->form == LDPC_FORM_SPLIT && !ldpc::is_single_edge(p->schedule))
+    return fail(LDPC_ERR_UNSUPPORTED, "the split form runs the single-edge schedules");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");
   // lane teams: a check (every schedule) or a variable (dynamic schedules) within one warp
@@ -659,8 +661,34 @@ ldpc_status_t ldpc_decode_ex(const ldpc_code_t* code, const void* llr, int64_t b
   // (FP32 WiFi-like code: 2.4-2.8x); tune bit 8 asks for it too
   const bool se_few = ldpc::is_single_edge(p->schedule) && fits &&
                       ((p->tune & 0x100) != 0 || (int64_t)228 * 1024 / ((int64_t)per + 1024) < 4);
-  const bool global_form = p->form == LDPC_FORM_GLOBAL || !fits || (p->form == LDPC_FORM_AUTO && se_few);
   void* scratch = nullptr;
+  // single-edge split form: the V region of a frame in shared memory, its edge
+  // arrays in a global slot; one CTA per SM holds as many frames as fit
+  const size_t vper = ldpc::is_single_edge(p->schedule) ? ldpc::se_vregion_bytes(arith, p->schedule, *g) : 0;
+  const int split_fpc = vper > 0 ? (int)std::min<int64_t>(16, ((int64_t)optin - gsm) / (int64_t)vper) : 0;
+  if (p->form == LDPC_FORM_SPLIT && split_fpc < 1)
+    return fail(LDPC_ERR_UNSUPPORTED, "the VN arrays of a frame exceed shared memory");
+  if (p->form == LDPC_FORM_SPLIT) {
+    int fpc = split_fpc;
+    if ((p->tune >> 2) & 3) fpc = std::min(fpc, 1 << ((p->tune >> 2) & 3));  // 2, 4 or 8 frames by request
+    if ((int64_t)fpc > batch) fpc = (int)batch;
+    const int64_t ctas = std::min<int64_t>((batch + fpc - 1) / fpc, (int64_t)sms);
+    const int64_t estride = ((int64_t)(per - vper) + 255) & ~(int64_t)255;
+    e = cudaMallocAsync(&scratch, (size_t)(ctas * fpc) * (size_t)estride, s);
+    if (e != cudaSuccess) return fail(LDPC_ERR_NOMEM, std::string("cudaMallocAsync(state): ") + cudaGetErrorString(e));
+    a.se_split = 1;
+    a.gstate = scratch;
+    a.gstate_stride = estride;
+    a.gstate_ctas = (int32_t)ctas;
+    a.frames_per_cta = fpc;
+    a.smem_per_frame = (int32_t)(((int64_t)vper + 15) & ~(int64_t)15);
+    e = ldpc::launch_se(a, arith, p->schedule, s);
+    const cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    return LDPC_OK;
+  }
+  const bool global_form = p->form == LDPC_FORM_GLOBAL || !fits || (p->form == LDPC_FORM_AUTO && se_few);
   a.smem_per_frame = (int32_t)per;
   if (global_form) {
     const int64_t stride = ((int64_t)per + 255) & ~(int64_t)255;

@@ -84,7 +84,7 @@ extern "C" ldpc_status_t ldpc_decode_noalloc(const ldpc_code_t* code, const void
     return fail(LDPC_ERR_INVALID_ARG, "q_step");
   if (ldpc::is_multi_edge(p->schedule) && (p->n_p <= 0 || p->n_p > 384 || p->n_g <= 0 || p->n_g > 255))
     return fail(LDPC_ERR_INVALID_ARG, "0 < n_p <= 384 and 0 < n_g <= 255 required");
-  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_CLUSTER || (p->tune & ~0x1ff) != 0 || (p->tune & 3) == 3)
+  if (p->form < LDPC_FORM_AUTO || p->form > LDPC_FORM_SPLIT || (p->tune & ~0x1ff) != 0 || (p->tune & 3) == 3)
     return fail(LDPC_ERR_INVALID_ARG, "bad form / tune");
   if (batch == 0) return LDPC_OK;
   if (!llr) return fail(LDPC_ERR_INVALID_ARG, "llr is NULL");

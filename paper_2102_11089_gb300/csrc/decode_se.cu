@@ -202,10 +202,11 @@ __device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, in
   if (blk) blk_note(s.Rblk, s.Rdirty, m, kold, bk);
 }
 
-// Decode one frame of code `gd` with its state at `base` (shared or global memory).
+// Decode one frame of code `gd` with the V region of its state at `vbase` and
+// the E region at `ebase` (shared or global memory; see SELayout).
 template <int A, int SCHED, class G>
 __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& gd, const G& g, const FrameIO& io,
-                                         unsigned char* base) {
+                                         unsigned char* vbase, unsigned char* ebase) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
@@ -216,19 +217,19 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   const int N = gd.N, E = gd.E, M = gd.M;
   const SELayout ly = se_layout(A, M, N, E, kNeedR);
   SEState<A> s;
-  s.C = (M_*)(base + ly.C);
-  s.P = (M_*)(base + ly.P);
-  s.lam = (L_*)(base + ly.lam);
-  s.L = (L_*)(base + ly.L);
-  s.D = (D_*)(base + ly.D);
-  s.Rmax = (M_*)(base + ly.Rmax);
-  s.Ridx = (int32_t*)(base + ly.Ridx);
-  s.par = (uint32_t*)(base + ly.par);
-  s.Dblk = (uint32_t*)(base + ly.Dblk);
-  s.Ddirty = (uint32_t*)(base + ly.Ddirty);
-  s.Rblk = (uint32_t*)(base + ly.Rblk);
-  s.Rdirty = (uint32_t*)(base + ly.Rdirty);
-  s.tab = (int16_t*)(base + ly.tab);
+  s.C = (M_*)(ebase + ly.C);
+  s.P = (M_*)(ebase + ly.P);
+  s.lam = (L_*)(vbase + ly.lam);
+  s.L = (L_*)(vbase + ly.L);
+  s.D = (D_*)(vbase + ly.D);
+  s.Rmax = (M_*)(vbase + ly.Rmax);
+  s.Ridx = (int32_t*)(vbase + ly.Ridx);
+  s.par = (uint32_t*)(vbase + ly.par);
+  s.Dblk = (uint32_t*)(vbase + ly.Dblk);
+  s.Ddirty = (uint32_t*)(vbase + ly.Ddirty);
+  s.Rblk = (uint32_t*)(vbase + ly.Rblk);
+  s.Rdirty = (uint32_t*)(vbase + ly.Rdirty);
+  s.tab = (int16_t*)(vbase + ly.tab);
   const float clip = a.llr_clip;
   const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
 
@@ -511,8 +512,9 @@ __global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
   const int warp = threadIdx.x >> 5;
   const int64_t b = (int64_t)blockIdx.x * a.frames_per_cta + warp;
   if (b >= a.batch) return;
-  se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4),
-                        smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame);
+  unsigned char* vbase = smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame;
+  se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase,
+                        vbase + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal);
 }
 
 // Global-memory form (frame state larger than shared memory): every warp owns
@@ -525,7 +527,26 @@ __global__ void __launch_bounds__(512) se_decode_kernel_gs(const DecodeArgs a) {
   const int64_t slot = (int64_t)blockIdx.x * a.frames_per_cta + warp;
   const int64_t slots = (int64_t)gridDim.x * a.frames_per_cta;
   unsigned char* base = (unsigned char*)a.gstate + slot * a.gstate_stride;
-  for (int64_t b = slot; b < a.batch; b += slots) se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), base);
+  unsigned char* ebase = base + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal;
+  for (int64_t b = slot; b < a.batch; b += slots)
+    se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), base, ebase);
+}
+
+// Split form: the V region of a frame (VN- and check-sized arrays) in shared
+// memory, its E region (the edge arrays) in a global-memory slot, small enough
+// in total for L2 to hold.  Every warp owns one slot and loops over the frames
+// b = slot + k * slots.
+template <int A, int SCHED, class G>
+__global__ void __launch_bounds__(512) se_decode_kernel_split(const DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
+  const int warp = threadIdx.x >> 5;
+  const int64_t slot = (int64_t)blockIdx.x * a.frames_per_cta + warp;
+  const int64_t slots = (int64_t)gridDim.x * a.frames_per_cta;
+  unsigned char* vbase = smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame;
+  unsigned char* ebase = (unsigned char*)a.gstate + slot * a.gstate_stride;
+  for (int64_t b = slot; b < a.batch; b += slots)
+    se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase, ebase);
 }
 
 // Queue form of the single-edge schedules: one warp per CTA takes work items
@@ -569,8 +590,9 @@ __global__ void __launch_bounds__(32) se_queue_kernel(const QueueArgs q) {
     io.trace = nullptr;
     io.max_updates = it.max_updates;
     io.frame = it.frame_index;
-    const int bytes = se_layout(A, s_gd.M, s_gd.N, s_gd.E, SCHED != kLMD).total;
-    se_frame<A, SCHED, QCGraph>(q.a, s_gd, g, io, bytes <= q.smem_state_bytes ? sstate : gslot);
+    const SELayout ly = se_layout(A, s_gd.M, s_gd.N, s_gd.E, SCHED != kLMD);
+    unsigned char* base = ly.total <= q.smem_state_bytes ? sstate : gslot;
+    se_frame<A, SCHED, QCGraph>(q.a, s_gd, g, io, base, base + ly.vtotal);
   }
 }
 
@@ -585,6 +607,14 @@ cudaError_t launch_se_queue_t(const QueueArgs& q, int grid, size_t smem, cudaStr
 
 template <int A, int S, class G>
 cudaError_t launch_one(const DecodeArgs& a, cudaStream_t st) {
+  if (a.se_split) {
+    const size_t smem = (size_t)a.graph_smem + (size_t)a.smem_per_frame * a.frames_per_cta;
+    auto k = se_decode_kernel_split<A, S, G>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k<<<(unsigned)a.gstate_ctas, 32 * a.frames_per_cta, smem, st>>>(a);
+    return cudaGetLastError();
+  }
   if (a.gstate) {
     const size_t smem = (size_t)a.graph_smem;
     auto k = se_decode_kernel_gs<A, S, G>;
@@ -634,6 +664,10 @@ cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem
 
 size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g) {
   return (size_t)se_layout(arith, g.M, g.N, g.E, sched != kLMD).total;
+}
+
+size_t se_vregion_bytes(int arith, int sched, const GraphDesc& g) {
+  return (size_t)se_layout(arith, g.M, g.N, g.E, sched != kLMD).vtotal;
 }
 
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s) {

@@ -80,7 +80,8 @@ struct DecodeArgs {
   int64_t gstate_stride;  // bytes per slot
   int32_t gstate_ctas;    // CTAs of the global-memory form
   int32_t frames_per_cta;
-  int32_t smem_per_frame;
+  int32_t smem_per_frame;  // shared-memory bytes per frame (single-edge split form: the V region)
+  int32_t se_split;        // single-edge split form: E regions in global slots of gstate_stride bytes
   int32_t graph_smem;    // bytes of staged graph tables at the start of shared memory
   int32_t team_w;        // lanes per check team: power of two >= max check degree
   int32_t cta_threads;   // multi-edge CTA size (256 or 512)
@@ -152,12 +153,18 @@ inline __host__ __device__ int graph_smem_bytes(const GraphDesc& d) {
   return d.tab_in_smem ? align16(d.tab_words * 4) : 0;
 }
 
-// Per-frame state layout of the single-edge (warp per frame) decoder.  Dblk /
-// Rblk: the largest metric key of each block of 32 VNs / 32 checks (the upper
-// level of the global argmax of CIRBP and RBP), with dirty bits of blocks
-// whose maximum may have dropped.
+// Per-frame state layout of the single-edge (warp per frame) decoder, in two
+// regions: the V region (VN- and check-sized arrays, `vtotal` bytes) and the E
+// region (the edge arrays C, P: offsets relative to its start, `etotal`
+// bytes).  Contiguous placement puts the E region right after the V region
+// (`total` bytes); the split form keeps the V region in shared memory and the
+// E region in global memory.  Dblk / Rblk: the largest metric key of each
+// block of 32 VNs / 32 checks (the upper level of the global argmax of CIRBP
+// and RBP), with dirty bits of blocks whose maximum may have dropped.
 struct SELayout {
-  int C, P, lam, L, D, Rmax, Ridx, par, Dblk, Ddirty, Rblk, Rdirty, tab, total;
+  int lam, L, D, Rmax, Ridx, par, Dblk, Ddirty, Rblk, Rdirty, tab, vtotal;
+  int C, P, etotal;
+  int total;
 };
 
 inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bool need_r) {
@@ -166,8 +173,6 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bo
   const int dv = arith == kINT6 ? 2 : 4;
   SELayout l;
   int o = 0;
-  l.C = o; o = align16(o + E * msg);
-  l.P = o; o = align16(o + E * msg);
   l.lam = o; o = align16(o + N * llr);
   l.L = o; o = align16(o + N * llr);
   l.D = o; o = align16(o + N * dv);
@@ -180,7 +185,12 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bo
   l.Rblk = o; o = align16(o + (need_r ? mb * 4 : 0));
   l.Rdirty = o; o = align16(o + (need_r ? ((mb + 31) / 32) * 4 : 0));
   l.tab = o; o = align16(o + (arith == kINT6 ? 256 * 2 : 0));
-  l.total = o;
+  l.vtotal = o;
+  o = 0;
+  l.C = o; o = align16(o + E * msg);
+  l.P = o; o = align16(o + E * msg);
+  l.etotal = o;
+  l.total = l.vtotal + l.etotal;
   return l;
 }
 
@@ -299,6 +309,7 @@ bool code_host_tab(const void* code, const int32_t* parts[5], int32_t sizes[5]);
 void set_error_detail(const std::string& why);  // text returned by ldpc_last_error_detail()
 
 size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g);
+size_t se_vregion_bytes(int arith, int sched, const GraphDesc& g);  // single-edge V region (split form)
 size_t flood_smem_per_frame(int arith, const GraphDesc& g);
 size_t me_smem_per_frame(int arith, int sched, const GraphDesc& g, int n_p, int n_g);  // big arrays
 size_t me_smem_per_cta(const GraphDesc& g, int n_p, int n_g);  // per-CTA working set

@@ -142,7 +142,10 @@ def test_decode_validation_needs_no_gpu(lib):
     q = L.make_params("lmd-cirbp", max_updates=10, form=L.FORM_CLUSTER)  # single-edge: no cluster form
     assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
                            null) == -5
-    q = L.make_params("me-cirbp", max_updates=10, form=4)
+    q = L.make_params("me-cirbp", max_updates=10, form=L.FORM_SPLIT)  # multi-edge: no split form
+    assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
+                           null) == -5
+    q = L.make_params("me-cirbp", max_updates=10, form=5)
     assert lib.ldpc_decode(code._h, dummy, 4, ctypes.byref(q), null, null, null, null, null,
                            null) == -1
     q = L.make_params("rbp", "int6", max_updates=10, q_step=0.0)

@@ -33,11 +33,15 @@ def test_global_form_equals_shared_form_and_oracle(schedule):
     g_g = run_gpu(code, q, torch, arith="int6", form=L.FORM_GLOBAL, **kw)
     for k in ["hard", "updates", "converged", "llr", "trace"]:
         assert np.array_equal(g_s[k], g_g[k]), k
+    if schedule not in ("flooding", "me-cirbp", "me-lmd-cirbp"):  # single-edge: VN arrays in smem, edges global
+        g_p = run_gpu(code, q, torch, arith="int6", form=L.FORM_SPLIT, **kw)
+        for k in ["hard", "updates", "converged", "llr", "trace"]:
+            assert np.array_equal(g_s[k], g_p[k]), k
     o = run_oracle(spec, q, "int6", **kw)
     assert_bitexact(g_g, o, schedule)
 
 
-@pytest.mark.parametrize("schedule", ["lmd-cirbp", "me-lmd-cirbp", "flooding"])
+@pytest.mark.parametrize("schedule", ["lmd-cirbp", "cirbp", "rbp", "lmdrbp", "me-lmd-cirbp", "flooding"])
 def test_global_form_fp32_wifi(schedule):
     spec = qc("wifi", 96)
     code = make_code(spec)
@@ -47,6 +51,21 @@ def test_global_form_fp32_wifi(schedule):
     g_g = run_gpu(code, lam, torch, arith="fp32", form=L.FORM_GLOBAL, **kw)
     for k in ["hard", "updates", "converged", "llr", "trace"]:
         assert np.array_equal(g_s[k], g_g[k]), k
+    if schedule not in ("flooding", "me-lmd-cirbp"):
+        for tune in (0, 1 << 2, 3 << 2):  # frames per CTA of the split form: as many as fit, 2, 8
+            g_p = run_gpu(code, lam, torch, arith="fp32", form=L.FORM_SPLIT, tune=tune, **kw)
+            for k in ["hard", "updates", "converged", "llr", "trace"]:
+                assert np.array_equal(g_s[k], g_p[k]), (tune, k)
+
+
+def test_split_form_refuses_other_schedules():
+    spec = regular96()
+    code = make_code(spec)
+    x = torch.zeros((1, 96), dtype=torch.float32, device="cuda:0")
+    for sch in ["flooding", "me-lmd-cirbp"]:
+        with pytest.raises(L.LdpcError) as e:
+            L.decode(code, x, schedule=sch, max_updates=10, form=L.FORM_SPLIT)
+        assert e.value.name == "LDPC_ERR_UNSUPPORTED"
 
 
 @pytest.mark.parametrize("schedule,n_p", [("lmd-cirbp", 0), ("me-lmd-cirbp", 64), ("me-cirbp", 64),
