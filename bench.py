@@ -578,6 +578,7 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
     ms_se, o_se = time_decode(L, code, x[:B3].contiguous(), p_se, reps=1)
     res["single_edge_lmd_cirbp"] = {"frames": B3, "fer": fer_of(o_se), "ms": ms_se,
                                     "gbit_s": B3 * code.K / (ms_se * 1e-3) / 1e9}
+    res["single_edge_forms"] = run_se_forms(args, L, code, device)
     if not args.no_sweep:
         res["sweep_config2"] = run_sweep(args, L, code, device)
         res["gamma_sweep_cirbp"] = run_gamma_sweep(args, L, code, device)
@@ -667,6 +668,34 @@ def run_sweep(args, L, code, device, ebn0s=(1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5
         del llr, of
     return {"workload": "wifi-like n2304, ME-LMD-CIRBP FP32, N_G 16, Eb/N0 x N_P x budget; flooding at equal "
                         "FER on the same frames", "points": rows, "seconds": time.perf_counter() - t_start}
+
+
+def run_se_forms(args, L, code, device, frames=8192, ebn0=1.5, budget_iters=3):
+    """The single-edge schedules (Algorithms 1 and 3, RBP) on the WiFi-like code in
+    their three execution forms: frame state in shared memory (two FP32 frames per
+    SM), in global memory (32 warps per SM), and split (VN and check arrays in
+    shared memory, edge arrays in global memory).  Results are identical in every
+    form (checked)."""
+    import torch
+    E, K = code.E, code.K
+    ebt = torch.full((frames,), ebn0, dtype=torch.float32, device=device)
+    llr, _ = L.awgn_llr(code, ebt, seed=7171, frame_offset=0)
+    rows = []
+    for sch in ("lmd-cirbp", "cirbp", "rbp"):
+        row = {"schedule": sch}
+        ref = None
+        for name, form in (("smem", L.FORM_SMEM), ("global", L.FORM_GLOBAL), ("split", L.FORM_SPLIT),
+                           ("auto", L.FORM_AUTO)):
+            p = L.make_params(sch, "fp32", gamma=0.1, max_updates=budget_iters * E, check_interval=1, form=form)
+            ms, o = time_decode(L, code, llr, p, reps=1)
+            if ref is None:
+                ref = o
+                row["fer"] = fer_of(o)
+            row[name] = {"ms": ms, "gbit_s": frames * K / (ms * 1e-3) / 1e9,
+                         "identical": all(torch.equal(ref[k], o[k]) for k in ref)}
+        rows.append(row)
+    return {"workload": f"wifi-like n2304, FP32, Eb/N0 {ebn0} dB, budget {budget_iters}E", "frames": frames,
+            "points": rows}
 
 
 def run_gamma_sweep(args, L, code, device, gammas=(0.0, 0.05, 0.1, 0.15, 0.2, 0.25, 0.3), frames=8192,

@@ -186,3 +186,28 @@ def test_cluster_form_bg1_z384_fp32_matches_oracle():
     assert np.array_equal(g["trace"][clean, :512], o["trace"][clean, :512])
     assert within_tol(g["c2v"][clean], o["state"]["C"][clean]).all()
     assert within_tol(g["pre"][clean], o["state"]["P"][clean]).all()
+
+
+def test_smem_stream_measures_a_plausible_peak():
+    # ldpc_smem_stream: the folded words are deterministic and the bandwidth lies
+    # between a quarter and 1.5x of 152 SMs x 128 B/clk at 2.07 GHz
+    dev = torch.device("cuda:0")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(sms * 2 * 1024, dtype=torch.int32, device=dev)
+    L.smem_stream(sms * 2, 1024, 64, sink)
+    torch.cuda.synchronize()
+    first = sink.clone()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    nbytes = L.smem_stream(sms * 2, 1024, 2048, sink)
+    b.record()
+    torch.cuda.synchronize()
+    assert nbytes == sms * 2 * 1024 * 2048 * 64
+    gbs = nbytes / (a.elapsed_time(b) * 1e-3) / 1e9
+    nominal = sms * 128 * 2.07e9 / 1e9
+    assert 0.25 * nominal < gbs < 1.5 * nominal, gbs
+    L.smem_stream(sms * 2, 1024, 64, sink)
+    torch.cuda.synchronize()
+    assert torch.equal(sink, first)
+    with pytest.raises(L.LdpcError):
+        L.smem_stream(1, 33, 1, sink)
