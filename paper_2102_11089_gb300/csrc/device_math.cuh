@@ -144,16 +144,17 @@ __device__ __forceinline__ int team_c2v(const G& g, const CA& C, const LA& L, in
   }
   // exclude-one combination: inclusive prefix and suffix scans over the team,
   // lane r takes prefix(r - 1) (+) suffix(r + 1); the sign is the team parity
-  // with r's own sign removed
+  // (one ballot) with r's own sign removed
+  const int team0 = (int)(threadIdx.x & 31) - r;  // first lane of the team
+  const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << team0);
   if (A == kFP32) {
     // idle lanes (e = j = 0) compute too and drop the value: no branch around phi
     const float enc0 = encode_fp((float)L[j] - (float)C[e], clip);
     const float enc = r < dc ? enc0 : 0.0f;
     const unsigned sg = __float_as_uint(enc) >> 31;
-    unsigned sall = sg;
+    const unsigned sall = __popc(__ballot_sync(kFull, sg) & tmask) & 1u;
     float pre = fabsf(enc), suf = pre;
     for (int o = 1; o < W; o <<= 1) {
-      sall ^= __shfl_xor_sync(kFull, sall, o);
       const float u = __shfl_up_sync(kFull, pre, o, W);
       const float d = __shfl_down_sync(kFull, suf, o, W);
       if (r >= o) pre += u;
@@ -166,10 +167,9 @@ __device__ __forceinline__ int team_c2v(const G& g, const CA& C, const LA& L, in
   } else {
     const int enc = r < dc ? (int)encode_int((int)L[j] - (int)C[e]) : 0;
     const unsigned sg = enc < 0;
-    unsigned sall = sg;
+    const unsigned sall = __popc(__ballot_sync(kFull, sg) & tmask) & 1u;
     int pre = r < dc ? abs(enc) : 31, suf = pre;
     for (int o = 1; o < W; o <<= 1) {
-      sall ^= __shfl_xor_sync(kFull, sall, o);
       const int u = __shfl_up_sync(kFull, pre, o, W);
       const int d = __shfl_down_sync(kFull, suf, o, W);
       if (r >= o) pre = min(pre, u);
