@@ -240,9 +240,8 @@ ldpc_status_t ldpc_encode(const ldpc_code_t *code, const uint8_t *info, int64_t 
  * Stops at a zero syndrome (checked per check_interval) or at the budget.
  * Execution form (params->form = LDPC_FORM_AUTO): frame state in shared
  * memory when it fits one CTA (single-edge frames: when shared memory holds
- * at least eight per SM; else CIRBP and RBP, which search every VN or check
- * each update, take the split form when shared memory holds two V regions,
- * and the other single-edge schedules global memory); else, for the multi-edge schedules and a batch
+ * at least eight per SM, else global memory; the split form only on request);
+ * else, for the multi-edge schedules and a batch
  * of at most twice the resident clusters (SMs / cluster size), spread over the
  * shared memory of a thread-block cluster (the smallest of 2, 4, 8 or 16 CTAs
  * that holds it and can be resident); else global memory.  A cluster size in

@@ -657,12 +657,9 @@ ldpc_status_t ldpc_decode_ex(const ldpc_code_t* code, const void* llr, int64_t b
   }
   if ((int64_t)cta_fixed + gsm > optin) return fail(LDPC_ERR_UNSUPPORTED, "working set exceeds shared memory");
   // single-edge frames (a warp each) that shared memory holds fewer than eight
-  // per SM run faster elsewhere (measured on the WiFi-like code, 1.5 dB, 3E):
-  // the schedules that search all VNs / checks every update (CIRBP, RBP) with
-  // their VN and check arrays in shared memory and the edge arrays in global
-  // memory (split form: 1.6-2.2x over either), the others with all state in
-  // global memory and 32 warps per SM (LMD-CIRBP: 1.5-2.3x); tune bit 8 asks
-  // for the global form
+  // per SM run faster with all state in global memory and 32 warps per SM
+  // (WiFi-like code, 1.5 dB, 3E: LMD-CIRBP 2.5x, CIRBP 1.7x, RBP 1.7x over two
+  // FP32 frames per SM; the split form ties or trails it); tune bit 8 asks for it too
   const int64_t smem_per_sm = (int64_t)228 * 1024 / ((int64_t)per + 1024);
   const bool se_few = ldpc::is_single_edge(p->schedule) && fits && ((p->tune & 0x100) != 0 || smem_per_sm < 8);
   void* scratch = nullptr;
@@ -672,10 +669,7 @@ ldpc_status_t ldpc_decode_ex(const ldpc_code_t* code, const void* llr, int64_t b
   const int split_fpc = vper > 0 ? (int)std::min<int64_t>(16, ((int64_t)optin - gsm) / (int64_t)vper) : 0;
   if (p->form == LDPC_FORM_SPLIT && split_fpc < 1)
     return fail(LDPC_ERR_UNSUPPORTED, "the VN arrays of a frame exceed shared memory");
-  const bool scans = p->schedule == LDPC_CIRBP || p->schedule == LDPC_RBP;
-  const bool auto_split = p->form == LDPC_FORM_AUTO && scans && (p->tune & 0x100) == 0 && split_fpc >= 2 &&
-                          (!fits || smem_per_sm < 8);
-  if (p->form == LDPC_FORM_SPLIT || auto_split) {
+  if (p->form == LDPC_FORM_SPLIT) {
     int fpc = split_fpc;
     if ((p->tune >> 2) & 3) fpc = std::min(fpc, 1 << ((p->tune >> 2) & 3));  // 2, 4 or 8 frames by request
     if ((int64_t)fpc > batch) fpc = (int)batch;

@@ -203,16 +203,18 @@ __device__ __forceinline__ void refresh_rmax(const G& g, const SEState<A>& s, in
 }
 
 // Decode one frame of code `gd` with the V region of its state at `vbase` and
-// the E region at `ebase` (shared or global memory; see SELayout).
-template <int A, int SCHED, class G>
+// the E region at `ebase` (shared or global memory; see SELayout).  kVs: the V
+// region is in shared memory, where the block maxima of the global argmaxes
+// pay (in global memory their atomics cost more than the plain scans save).
+template <int A, int SCHED, class G, bool kVs>
 __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& gd, const G& g, const FrameIO& io,
                                          unsigned char* vbase, unsigned char* ebase) {
   using M_ = typename Arith<A>::msg;
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   constexpr bool kNeedR = SCHED != kLMD;
-  constexpr bool kDblk = SCHED == kCIRBP;                     // global argmax of D every update
-  constexpr bool kRblk = SCHED == kCIRBP || SCHED == kRBP;    // global argmax of the residuals
+  constexpr bool kDblk = kVs && SCHED == kCIRBP;                   // global argmax of D every update
+  constexpr bool kRblk = kVs && (SCHED == kCIRBP || SCHED == kRBP);  // global argmax of the residuals
   const int lane = threadIdx.x & 31;
   const int N = gd.N, E = gd.E, M = gd.M;
   const SELayout ly = se_layout(A, M, N, E, kNeedR);
@@ -321,7 +323,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     // -- selection
     int eglob = -1;  // RBP / CIRBP fallback: the global residual argmax fixes e*
     if (SCHED == kRBP) {
-      eglob = global_argmax_R_blk<A>(M, s);
+      eglob = kRblk ? global_argmax_R_blk<A>(M, s) : global_argmax_R<A>(M, s);
       nstar = g.evn(eglob);
     } else if (kLMDR) {
       if (enext < 0) {  // Alg. 2 line 3, and an empty candidate set
@@ -333,10 +335,10 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
       }
     } else if (SCHED == kCIRBP) {
       uint32_t dkey;
-      nstar = global_argmax_D_blk<A>(N, s, dkey);
+      nstar = kDblk ? global_argmax_D_blk<A>(N, s, dkey) : global_argmax_D<A>(N, s, dkey);
       const bool fallback = (A == kFP32) ? (__uint_as_float(dkey) < a.gamma_f) : ((int)dkey < a.gamma_i);
       if (fallback) {  // Alg. 1 line 6
-        eglob = global_argmax_R_blk<A>(M, s);
+        eglob = kRblk ? global_argmax_R_blk<A>(M, s) : global_argmax_R<A>(M, s);
         nstar = g.evn(eglob);
         ++nfall;
       }
@@ -513,8 +515,8 @@ __global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
   const int64_t b = (int64_t)blockIdx.x * a.frames_per_cta + warp;
   if (b >= a.batch) return;
   unsigned char* vbase = smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame;
-  se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase,
-                        vbase + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal);
+  se_frame<A, SCHED, G, true>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase,
+                              vbase + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal);
 }
 
 // Global-memory form (frame state larger than shared memory): every warp owns
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(512) se_decode_kernel_gs(const DecodeArgs a) {
   unsigned char* base = (unsigned char*)a.gstate + slot * a.gstate_stride;
   unsigned char* ebase = base + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal;
   for (int64_t b = slot; b < a.batch; b += slots)
-    se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), base, ebase);
+    se_frame<A, SCHED, G, false>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), base, ebase);
 }
 
 // Split form: the V region of a frame (VN- and check-sized arrays) in shared
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(512) se_decode_kernel_split(const DecodeArgs a
   unsigned char* vbase = smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame;
   unsigned char* ebase = (unsigned char*)a.gstate + slot * a.gstate_stride;
   for (int64_t b = slot; b < a.batch; b += slots)
-    se_frame<A, SCHED, G>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase, ebase);
+    se_frame<A, SCHED, G, true>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase, ebase);
 }
 
 // Queue form of the single-edge schedules: one warp per CTA takes work items
@@ -592,7 +594,7 @@ __global__ void __launch_bounds__(32) se_queue_kernel(const QueueArgs q) {
     io.frame = it.frame_index;
     const SELayout ly = se_layout(A, s_gd.M, s_gd.N, s_gd.E, SCHED != kLMD);
     unsigned char* base = ly.total <= q.smem_state_bytes ? sstate : gslot;
-    se_frame<A, SCHED, QCGraph>(q.a, s_gd, g, io, base, base + ly.vtotal);
+    se_frame<A, SCHED, QCGraph, false>(q.a, s_gd, g, io, base, base + ly.vtotal);
   }
 }
 
