@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--queue-frames", type=int, default=6144,
                     help="frames of the mixed-lifting BG2-shaped queue comparison (extras)")
+    ap.add_argument("--queue-stream", type=int, default=0,
+                    help="stream this many mixed-lifting frames through one persistent queue launch and print "
+                         "its JSON (config 3 at its stated size: 1000000)")
     ap.add_argument("--queue-only", action="store_true",
                     help="run only the mixed-lifting queue comparison and print its JSON")
     ap.add_argument("--large-frames", type=int, default=304,
@@ -586,6 +589,7 @@ def run_extras(args, L, code, device, stream, fer_ci, budget, value):
         res["queue_mixed_bg2"] = run_queue_mixed(args, L, device)
     if args.large_frames > 0:
         res["large_bg1_z384"] = run_large_bg1(args, L, device)
+        res["large_bg1_ebn0_sweep"] = run_large_sweep(args, L, device)
     res["weighted_bp_config4"] = run_wbp_config4(args, L, device)
     # Properties 1 and 2 (Sec. 3.A) on flooding: empirical J(gamma), F(gamma) at
     # gamma = 0, 0.1, ..., 0.9 for iterations 0-2 (analogue of the paper's Fig. 1b)
@@ -929,6 +933,82 @@ def run_large_bg1(args, L, device, frames=None, reps=2, points=None):
     return res
 
 
+def run_large_sweep(args, L, device, frames=1216, ebn0s=(0.8, 1.0, 1.2, 1.4, 1.6)):
+    """The 26,112-bit BG1-shaped code over Eb/N0 0.8-1.6 dB (ME-LMD-CIRBP, budget
+    5E, FP32 at N_P = 64 and 256, 6-bit at N_P = 256; default form): FER and
+    decoded Gbit/s on a bounded batch per point (four waves of the global-memory
+    form) in place of the HBM-sized batch."""
+    import torch
+    from paper_2102_11089_gb300 import workloads as wl
+    d = wl.bg1_like(5)
+    code = L.Code.from_protograph(d.shifts(384), 384, d.info_cols * 384, d.punct_cols)
+    rows = []
+    for eb in ebn0s:
+        ebt = torch.full((frames,), eb, dtype=torch.float32, device=device)
+        lam, q = L.awgn_llr(code, ebt, seed=3131, frame_offset=0, quantize=True)
+        for arith, n_p in (("fp32", 64), ("fp32", 256), ("int6", 256)):
+            x = q if arith == "int6" else lam
+            p = L.make_params("me-lmd-cirbp", arith, gamma=0.1, n_p=n_p, n_g=16, max_updates=5 * code.E,
+                              check_interval=1, seed=1234)
+            ms, o = time_decode(L, code, x, p, reps=1)
+            errs = frame_errors(o)
+            rows.append({"ebn0_db": eb, "arith": arith, "n_p": n_p, "fer": errs / frames,
+                         "fer_ci95": list(clopper_pearson(errs, frames)), "ms": ms,
+                         "gbit_s": frames * code.K / (ms * 1e-3) / 1e9,
+                         "mean_updates": float(o["updates"].float().mean().item())})
+        del lam, q
+    return {"workload": "bg1-like 46x68, Z=384, n=26112, budget 5E, ME-LMD-CIRBP", "frames_per_point": frames,
+            "points": rows}
+
+
+def run_queue_stream(args, L, device, frames):
+    """Config 3 at its stated size: `frames` mixed-lifting BG2-shaped frames (Z
+    uniform over 16..384, Eb/N0 ~ U[0.5, 3.0] dB, budget ~ U{2..20}E per frame)
+    streamed through one persistent queue launch (items in decreasing-budget
+    order, autotuned launch shape); FER and decoded Gbit/s."""
+    import tempfile
+    import torch
+    from paper_2102_11089_gb300 import autotune as at
+    w = mixed_bg2(L, device, frames, "fp32")
+    codes, zi = w["codes"], w["zi"]
+    p = L.make_params("me-lmd-cirbp", "fp32", gamma=0.1, n_p=args.n_p, n_g=args.n_g, check_interval=1, seed=1234)
+    lpt = np.argsort(-w["budget"].astype(np.float64), kind="stable")
+    items = L.make_items(zi[lpt], w["off"][lpt], w["off"][lpt], w["budget"][lpt], lpt, device=device)
+    hard = torch.empty(w["total"], dtype=torch.uint8, device=device)
+    upd = torch.empty(frames, dtype=torch.int64, device=device)
+    conv = torch.empty(frames, dtype=torch.uint8, device=device)
+    nc = min(frames, 4096)
+    cal = L.make_items(zi[lpt[:nc]], w["off"][lpt[:nc]], w["off"][lpt[:nc]], w["budget"][lpt[:nc]], lpt[:nc],
+                       device=device)
+    with tempfile.TemporaryDirectory() as dd:
+        p.tune = at.tune_queue(codes, cal, nc, w["llr"], p, hard=hard, updates=upd, converged=conv,
+                               cache=at.TuneCache(os.path.join(dd, "tune.json")), repeats=1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    L.decode_queue(codes, items, frames, w["llr"], p, hard=hard, updates=upd, converged=conv,
+                   mode=L.QUEUE_PERSISTENT)
+    b.record()
+    torch.cuda.synchronize()
+    L.sync()
+    ms = a.elapsed_time(b)
+    # frame errors: any decided bit of a frame set (all-zero codeword), per Z block
+    errs = 0
+    hb = hard.cpu().numpy()
+    Ns = np.array([c.N for c in codes])
+    for ci in range(len(codes)):
+        idx = np.nonzero(zi == ci)[0]
+        if len(idx) == 0:
+            continue
+        o0 = int(w["off"][idx[0]])
+        errs += int(hb[o0:o0 + len(idx) * Ns[ci]].reshape(len(idx), Ns[ci]).any(axis=1).sum())
+    return {"workload": "bg2-like 42x52, Z~U{16..384}, Eb/N0~U[0.5,3] dB, budget~U{2..20}E per frame",
+            "frames": frames, "launches": 1, "ms": ms, "gbit_s": w["info_bits"] / (ms * 1e-3) / 1e9,
+            "fer": errs / frames, "fer_ci95": list(clopper_pearson(errs, frames)),
+            "mean_updates_per_frame": float(upd.float().mean().item()), "tune": at.describe(p.tune),
+            "llr_gb": w["total"] * 4 / 1e9}
+
+
 def run_wbp_config4(args, L, device, frames=4096, reps=2):
     """Weighted BP and its adjoint (12x24 protograph, Z=24: n=576), T = 8E
     updates of an LMD-CIRBP schedule recorded at 2.0 dB, 4,096 frames: time of
@@ -997,6 +1077,13 @@ def run_decode_only(args):
 
 def main():
     args = parse()
+    if args.queue_stream > 0:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2102_11089_gb300 as L
+        print(json.dumps(run_queue_stream(args, L, torch.device("cuda", 0), args.queue_stream)))
+        return
     if args.queue_only:
         import torch
         import __graft_entry__
