@@ -22,11 +22,19 @@
 //           phase with atomic deltas; integer sums do not depend on the order
 //           of the updates.  L~_j = lambda_j + that sum (x 2^-k).
 //
-// Algorithm 4 keeps the group index floor(D N_G) of every VN in shared memory.
-// Its random fill takes the fill-group members with the smallest keys (word
-// n mod 4 of Philox4x32-10 with counter (n/4, step, frame), key = seed; equal
-// keys to the lower index): members with key <= T are gathered (T bisected
-// until between `need` and kCap of them), then ranked exactly.
+// Algorithm 4 keeps the group index floor(D N_G) of every VN in shared memory
+// and the group sizes up to date.  Its random fill takes the fill-group members
+// with the smallest keys (word n mod 4 of Philox4x32-10 with counter (n/4,
+// step, frame), key = seed; equal keys to the lower index): members with key
+// <= T are gathered (T bisected until between `need` and kCap of them), then
+// ranked exactly.
+//
+// Selection lists: the VNs of the next step (P' of Algorithm 6, Algorithm 4's
+// top groups and fill winners) are appended to the other of two lists by slot
+// atomics as they are chosen, in no particular order; every consumer is
+// order-independent.  A VN's rank in index order (its trace position, and
+// whether the budget keeps it in a truncated last step) is counted only when
+// a trace is requested or the step is truncated.
 #include <cooperative_groups.h>
 
 #include <algorithm>
