@@ -1,7 +1,7 @@
 """Parity at the benchmark's full size and launch configuration.
 
-The bench decodes 65,536 frames of the WiFi-like n = 2304 code at Eb/N0 2.0 dB with
-ME-LMD-CIRBP (N_P 64, N_G 16, budget 5E, syndrome after every step) in one
+The bench decodes 65,536 frames of the WiFi-like n = 2304 code at Eb/N0 1.5 dB with
+ME-LMD-CIRBP (N_P 64, N_G 16, budget 3E, syndrome after every step) in one
 `ldpc_decode` launch, default form.  Here the same launch runs on seeded inputs
 (shared generator), with the edge trace requested (stores only: the schedule
 and results are those of the timed launch), and is checked
@@ -9,7 +9,8 @@ and results are those of the timed launch), and is checked
   * on sampled frames against the oracle, run frame by frame with the same frame
     index (the random fill of Algorithm 4 is keyed by it): 6-bit mode bit-exact
     (trace, updates, decisions, final LLRs); FP32 traces equal up to the oracle's
-    first near-tie, decisions and convergence equal;
+    first near-tie, and decisions and convergence equal for the frames that meet
+    none (beyond a near-tie FP32 and FP64 may legitimately part);
   * on every frame by properties that hold at any size: a frame is reported
     converged exactly when its decisions satisfy every check, the decisions are
     the signs of the final LLRs, and the budget bounds the update count (a frame
@@ -31,7 +32,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 BATCH = 65536
-EBN0 = 2.0
+EBN0 = 1.5
 SEED_IN = 2102
 KW = dict(schedule="me-lmd-cirbp", n_p=64, n_g=16, check_interval=1, seed=1234, gamma=0.1)
 
@@ -53,7 +54,7 @@ def _syndrome_ok(spec, hard):
 def _run(arith):
     spec = qc("wifi", 96)
     code = make_code(spec)
-    budget = 5 * code.E
+    budget = 3 * code.E
     lam = wl.seeded_llrs(code.N, BATCH, wl.sigma2_from_ebn0(EBN0, rate(spec)), SEED_IN)
     x = wl.quantize_llrs(lam, 0.5) if arith == "int6" else lam
     dev = torch.device("cuda:0")
@@ -103,15 +104,19 @@ def test_bench_workload_int6_sampled_frames_bitexact():
 def test_bench_workload_fp32_sampled_frames_match_oracle():
     spec, code, budget, x, idx, g = _run("fp32")
     _whole_batch_properties(spec, budget, g)
-    assert (g["converged"] & 1).mean() > 0.99  # FER 0 at this operating point (oracle: 4,096 frames)
+    assert (g["converged"] & 1).mean() > 0.97  # FER about 1 % at this operating point
     matched = []
     for r, b in enumerate(idx):
         o = _oracle_frame(spec, x, b, "fp32", budget)
-        assert int(g["converged"][b] & 1) == int(o["converged"][0]), f"frame {b}: converged"
-        assert np.array_equal(g["hard"][b], o["hard"][0]), f"frame {b}: decisions"
         u = int(min(o["updates"][0], g["updates"][b]))
-        tie = np.flatnonzero(o["gap"][0, :u] < NEAR_TIE)
-        lim = int(tie[0]) if len(tie) else u
+        tie = np.flatnonzero(o["gap"][0, :int(o["updates"][0])] < NEAR_TIE)
+        if len(tie) == 0:
+            assert int(g["converged"][b] & 1) == int(o["converged"][0]), f"frame {b}: converged"
+            assert np.array_equal(g["hard"][b], o["hard"][0]), f"frame {b}: decisions"
+        elif (g["converged"][b] & 1) and o["converged"][0]:
+            # both found a codeword by different paths: the same one
+            assert np.array_equal(g["hard"][b], o["hard"][0]), f"frame {b}: decisions"
+        lim = int(tie[0]) if len(tie) and tie[0] < u else u
         gt, ot = g["trace"][r, :lim], o["trace"][0, :lim]
         assert np.array_equal(gt, ot), f"frame {b}: trace differs before the first near-tie at {lim}"
         matched.append(lim)
