@@ -12,10 +12,15 @@
 //     exclude-one C2V of eq. (2) (or min-sum) by width-W shuffles, then
 //     L~_j and D_j (eq. 8) of j in N(i)\n*, which are also the LMD candidates
 //     (LMD-CIRBP by D_j, LMDRBP by the new residuals of those edges).
-// Per-frame state in shared memory:
-//   C[E] L^C, P[E] L~^C, lam/L[N], D[N], Rmax/Ridx[M] (largest residual per
-//   check, for the global argmax of eq. (5): RBP and CIRBP's fallback), par
-//   (syndrome bits of the tentative decisions bsgn(L), Sec. 2.A).
+// Per-frame state (SELayout): the V region lam/L[N], D[N], Rmax/Ridx[M]
+// (largest residual per check, for the global argmax of eq. (5): RBP and
+// CIRBP's fallback), par (syndrome bits of the tentative decisions bsgn(L),
+// Sec. 2.A) and the block maxima of D and Rmax; the E region C[E] L^C, P[E]
+// L~^C.  Forms: both regions in shared memory (several frames per CTA), both in
+// a global slot, or the V region in shared memory and the E region in a global
+// slot (split form).  Where the V region is in shared memory, CIRBP's and RBP's
+// global argmaxes read the block maxima (one key per 32 VNs or checks, kept
+// exact) and one block instead of every entry.
 // The graph is a QCGraph (protograph arithmetic) or TabGraph (CSR tables), both
 // staged once per CTA in shared memory.
 #include "device_math.cuh"
