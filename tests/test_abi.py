@@ -266,3 +266,21 @@ def test_build_regular_rejects_bad_shapes(lib):
         with pytest.raises(L.LdpcError) as e:
             L.Code.regular(*args, 1)
         assert e.value.name == "LDPC_ERR_INVALID_ARG"
+
+
+def test_decode_ex_validation_needs_no_gpu(lib):
+    # ldpc_decode_ex: outputs struct required; flooding keeps no L~^C (pre_out);
+    # the split form runs only the single-edge schedules
+    c, v, m = wl.regular_code(96, 3, 6, 1)
+    code = L.Code.from_edges(c, v, m, 96, 48)
+    dummy = ctypes.c_void_p(16)
+    o = L.DecodeOutputs()
+    p = L.make_params("flooding", max_updates=288)
+    assert lib.ldpc_decode_ex(code._h, dummy, 4, ctypes.byref(p), None, None) == -1
+    o.pre_out = 16
+    assert lib.ldpc_decode_ex(code._h, dummy, 4, ctypes.byref(p), ctypes.byref(o), None) == -1
+    assert lib.ldpc_decode_ex(code._h, dummy, 0, ctypes.byref(L.make_params("cirbp", max_updates=9)),
+                              ctypes.byref(o), None) == 0  # batch 0: no-op
+    q = L.make_params("flooding", max_updates=288, form=L.FORM_SPLIT)
+    assert lib.ldpc_decode_ex(code._h, dummy, 4, ctypes.byref(q), ctypes.byref(L.DecodeOutputs()), None) == -5
+    assert ctypes.sizeof(L.DecodeOutputs) == 8 * ctypes.sizeof(ctypes.c_void_p)
