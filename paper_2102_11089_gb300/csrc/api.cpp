@@ -878,7 +878,10 @@ ldpc_status_t wbp_setup(const ldpc_code_t* code, const float* llr, int64_t batch
   a->graph_smem = ldpc::graph_smem_bytes(*g);
   a->frame_bytes = ldpc::wbp_state_bytes(*g, backward);
   const int64_t room = (int64_t)max_optin_smem() - a->graph_smem;
-  const int64_t f = std::min<int64_t>(8, std::min<int64_t>(batch, room / a->frame_bytes));
+  // frames (warps) per CTA: as many as shared memory holds for the adjoint (a
+  // serial chain per frame: more resident warps pay; 11 frames of the n = 576
+  // code: -21 %), at most 8 for the forward (more gained nothing there)
+  const int64_t f = std::min<int64_t>(backward ? 16 : 8, std::min<int64_t>(batch, room / a->frame_bytes));
   if (f < 1) return fail(LDPC_ERR_UNSUPPORTED, "frame state exceeds shared memory");
   *fpc = (int)f;
   return LDPC_OK;

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) wbp_forward_kernel(const WbpArgs a) {
 }
 
 template <class G>
-__global__ void __launch_bounds__(256) wbp_backward_kernel(const WbpArgs a) {
+__global__ void __launch_bounds__(512) wbp_backward_kernel(const WbpArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const G g = GraphStage<G>::make(a.g, (int32_t*)smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
