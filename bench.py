@@ -615,7 +615,7 @@ def frame_errors(out):
 
 
 def run_sweep(args, L, code, device, ebn0s=(1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5), nps=(4, 16, 64),
-              budgets=(1, 2, 3, 5), frames=65536, frames_np4=16384):
+              budgets=(1, 2, 3, 5, 10), frames=65536, frames_np4=16384):
     """The WiFi-like code over Eb/N0 x N_P x budget (ME-LMD-CIRBP, FP32), each
     point against flooding BP at equal FER on the same frames.
 
@@ -629,6 +629,7 @@ def run_sweep(args, L, code, device, ebn0s=(1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5
     import torch
     E, K = code.E, code.K
     rows = []
+    variants = []
     flood_ms_cache = {}
     t_start = time.perf_counter()
     for eb in ebn0s:
@@ -669,9 +670,20 @@ def run_sweep(args, L, code, device, ebn0s=(1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5
                     row["flood_equal_fer"] = {"iterations": istar, "fer": fsub[istar], "ms": fms, "gbit_s": fg}
                     row["ci_over_flood"] = row["ci_gbit_s"] / fg
                 rows.append(row)
+        if eb == 1.5:  # the other multi-edge settings of the config at the headline point
+            for sch, n_p, n_g in (("me-cirbp", 64, 16), ("me-lmd-cirbp", 64, 4), ("me-lmd-cirbp", 64, 8)):
+                p = L.make_params(sch, "fp32", gamma=0.1, n_p=n_p, n_g=n_g, max_updates=3 * E, check_interval=1,
+                                  seed=1234)
+                ms, o = time_decode(L, code, llr, p, reps=1)
+                errs = frame_errors(o)
+                variants.append({"schedule": sch, "n_p": n_p, "n_g": n_g, "ebn0_db": eb, "budget_iters": 3,
+                                 "frames": B, "fer": errs / B, "fer_ci95": list(clopper_pearson(errs, B)),
+                                 "ms": ms, "gbit_s": B * K / (ms * 1e-3) / 1e9,
+                                 "mean_updates": float(o["updates"].float().mean().item())})
         del llr, of
     return {"workload": "wifi-like n2304, ME-LMD-CIRBP FP32, N_G 16, Eb/N0 x N_P x budget; flooding at equal "
-                        "FER on the same frames", "points": rows, "seconds": time.perf_counter() - t_start}
+                        "FER on the same frames", "points": rows, "variants": variants,
+            "seconds": time.perf_counter() - t_start}
 
 
 def run_se_forms(args, L, code, device, frames=8192, ebn0=1.5, budget_iters=3):
