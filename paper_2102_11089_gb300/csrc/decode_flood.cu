@@ -65,10 +65,9 @@ __device__ __forceinline__ void flood_frame(const DecodeArgs& a, const G& g, int
     return __syncthreads_or(any);
   };
 
-  int64_t count = 0;
+  int64_t count = 0, left = a.check_interval;
   bool ok = a.check_interval > 0 && !syndrome_nonzero();
   while (!ok && count + E <= a.max_updates) {
-    const int64_t before = count;
     for (int t0 = warp * tpw; t0 < M; t0 += nw * tpw) {  // every C2V from the previous V2C
       const int m = t0 + team;
       int e, j;
@@ -80,8 +79,7 @@ __device__ __forceinline__ void flood_frame(const DecodeArgs& a, const G& g, int
     for (int n = tid; n < N; n += nt) L[n] = vn_total<A, G>(g, lam, C, n);  // eq. (3)
     __syncthreads();
     count += E;
-    if (a.check_interval > 0 && (count / a.check_interval) > (before / a.check_interval))
-      ok = !syndrome_nonzero();
+    if (check_due(left, a.check_interval, E)) ok = !syndrome_nonzero();
   }
   const int conv = !syndrome_nonzero();
   for (int n = tid; n < N; n += nt) {

@@ -265,11 +265,12 @@ __device__ void alg4(const X& x, const MEState<A, X>& s, int N, int np, int ng, 
   if (need > 0) {
     // first threshold: need + 3 sqrt(need) + 8 expected members at or below
     // it, short of `need` with probability < 1e-3 (the selection does not
-    // depend on it)
+    // depend on it, so approximate arithmetic serves)
     const int members = s.cnt[fg] - s.cntS[fg];
-    const float want = (float)need + 3.0f * sqrtf((float)need) + 8.0f;
+    const float fn = (float)need;
+    const float want = fn + 3.0f * fn * rsqrtf(fn) + 8.0f;
     if ((float)members > want) {
-      const float t = want / (float)members * 4294967296.0f;
+      const float t = __fdividef(want, (float)members) * 4294967296.0f;
       thr0 = t >= 4294967040.0f ? 0xffffffffu : (uint32_t)t;
     }
   }
@@ -538,7 +539,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
   }
   x.sync();
 
-  int64_t count = 0;
+  int64_t count = 0, left = a.check_interval;
   uint32_t step = 0;
   int cur = 0;  // selection buffer of this step (s.sel[cur * np ...], ms->nsel[cur])
   bool stop = a.check_interval > 0 && ms->unsat == 0;
@@ -759,9 +760,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     if (tid == 0) ms->ncnu = 0;
     count += done;
     ++step;
-    if (a.check_interval > 0 && (count / a.check_interval) > ((count - done) / a.check_interval) &&
-        ms->unsat == 0)
-      break;
+    if (check_due(left, a.check_interval, done) && ms->unsat == 0) break;
     if (count >= io.max_updates) break;
     if constexpr (SCHED == kMECIRBP) {  // the selection bitmap is still clear from this step's start
       alg4<A, X>(x, s, N, np, ng, 0, step, frame, a.seed, sn, &ms->nsel[cur ^ 1]);  // Alg. 5 line 4

@@ -316,7 +316,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
 
   // ---- schedule loop
   constexpr bool kLMDR = SCHED == kLMDRBP || SCHED == kSLMDRBP;
-  int64_t count = 0, nfall = 0;
+  int64_t count = 0, nfall = 0, left = a.check_interval;
   int nstar = 0;
   int enext = -1;  // LMDRBP: edge found by Alg. 2 line 9 for the next update (-1: none)
   bool stop = (a.check_interval > 0 && unsat == 0);
@@ -457,7 +457,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     __syncwarp();
 
     ++count;
-    if (a.check_interval > 0 && (count % a.check_interval) == 0 && unsat == 0) break;
+    if (check_due(left, a.check_interval, 1) && unsat == 0) break;
 
     // -- LMDRBP: next edge = argmax of the residuals just refreshed (Alg. 2 line
     //    9), or over the edges of m* to N(m*)\n* when d_v(n*) = 1 (Sec. 5.A);

@@ -93,6 +93,22 @@ __device__ __forceinline__ uint16_t ci_int(int a, int b, const int16_t* tab) {
   return (uint16_t)(d < 0 ? -d : d);
 }
 
+// Syndrome-check cadence without a 64-bit division per step: `left` counts the
+// updates until the next multiple of `interval` (1..interval; start it at
+// interval).  Advances by `done` updates (0 <= done < 2^31) and returns true
+// when a multiple of interval was reached, i.e. floor(count / interval) grew.
+__device__ __forceinline__ bool check_due(int64_t& left, int64_t interval, int64_t done) {
+  if (interval <= 0) return false;
+  if (done < left) {
+    left -= done;
+    return false;
+  }
+  int64_t rest = done - left;  // updates past the first multiple reached
+  if (rest >= interval) rest = (int64_t)((uint32_t)rest % (uint32_t)interval);  // here interval <= rest < 2^31
+  left = interval - rest;
+  return true;
+}
+
 // Order-preserving 32-bit keys of non-negative metric values.
 __device__ __forceinline__ uint32_t mkey(float v) { return __float_as_uint(v); }
 __device__ __forceinline__ uint32_t mkey(int v) { return (uint32_t)v; }
@@ -142,9 +158,8 @@ __device__ __forceinline__ int team_c2v(const G& g, const CA& C, const LA& L, in
       j = g.cvn(cc, r);
     }
   }
-  // exclude-one combination: inclusive prefix and suffix scans over the team,
-  // lane r takes prefix(r - 1) (+) suffix(r + 1); the sign is the team parity
-  // (one ballot) with r's own sign removed
+  // exclude-one combination by one butterfly over the team; the sign is the
+  // team parity (one ballot) with r's own sign removed
   const int team0 = (int)(threadIdx.x & 31) - r;  // first lane of the team
   const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << team0);
   if (A == kFP32) {
@@ -153,31 +168,37 @@ __device__ __forceinline__ int team_c2v(const G& g, const CA& C, const LA& L, in
     const float enc = r < dc ? enc0 : 0.0f;
     const unsigned sg = __float_as_uint(enc) >> 31;
     const unsigned sall = __popc(__ballot_sync(kFull, sg) & tmask) & 1u;
-    float pre = fabsf(enc), suf = pre;
+    // the team's largest phi mx and the sum `rest` of the others (one copy of
+    // mx left out): the sum over the other lanes is rest for a lane holding mx,
+    // else (rest - phi_r) + mx, whose subtraction loses at most an ulp of
+    // phi_r <= mx against a result >= mx (no cancellation of a dominant term;
+    // phi = +inf for a zero input gives inf or the finite rest, never inf - inf)
+    const float a0 = fabsf(enc);
+    float mx = a0, rest = 0.0f;
     for (int o = 1; o < W; o <<= 1) {
-      const float u = __shfl_up_sync(kFull, pre, o, W);
-      const float d = __shfl_down_sync(kFull, suf, o, W);
-      if (r >= o) pre += u;
-      if (r + o < W) suf += d;
+      const float omx = __shfl_xor_sync(kFull, mx, o, W);
+      const float ore = __shfl_xor_sync(kFull, rest, o, W);
+      rest = (rest + ore) + fminf(mx, omx);
+      mx = fmaxf(mx, omx);
     }
-    const float pl = __shfl_up_sync(kFull, pre, 1, W);
-    const float sr = __shfl_down_sync(kFull, suf, 1, W);
-    const float sum = (r > 0 ? pl : 0.0f) + (r + 1 < W ? sr : 0.0f);
+    const float sum = a0 == mx ? rest : (rest - a0) + mx;
     out = (typename Arith<A>::msg)combine_fp(sum, sall ^ sg, clip);
   } else {
     const int enc = r < dc ? (int)encode_int((int)L[j] - (int)C[e]) : 0;
     const unsigned sg = enc < 0;
     const unsigned sall = __popc(__ballot_sync(kFull, sg) & tmask) & 1u;
-    int pre = r < dc ? abs(enc) : 31, suf = pre;
+    // the team's smallest and second smallest magnitudes (idle lanes: 31),
+    // packed in one word: the minimum over the other lanes is m2 for a lane
+    // holding m1, else m1
+    const int a0 = r < dc ? abs(enc) : 31;
+    int m1 = a0, m2 = 31;
     for (int o = 1; o < W; o <<= 1) {
-      const int u = __shfl_up_sync(kFull, pre, o, W);
-      const int d = __shfl_down_sync(kFull, suf, o, W);
-      if (r >= o) pre = min(pre, u);
-      if (r + o < W) suf = min(suf, d);
+      const int pk = __shfl_xor_sync(kFull, m1 | (m2 << 8), o, W);
+      const int o1 = pk & 0xff, o2 = pk >> 8;
+      m2 = min(max(m1, o1), min(m2, o2));
+      m1 = min(m1, o1);
     }
-    const int pl = __shfl_up_sync(kFull, pre, 1, W);
-    const int sr = __shfl_down_sync(kFull, suf, 1, W);
-    const int mag = min(r > 0 ? pl : 31, r + 1 < W ? sr : 31);
+    const int mag = a0 == m1 ? m2 : m1;
     out = (typename Arith<A>::msg)((sall ^ sg) ? -mag : mag);
   }
   return dc;
