@@ -698,17 +698,30 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     // have passed the commit barrier now
     for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     // -- precomputed C2V of every affected check (once per check); the L~ sums
-    //    of its variables follow by exact deltas
-    for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
-      const int t = t0 + team;
-      const int m = t < ncu ? s.cul[t] : -1;
-      int e, j;
-      M_ out;
-      const int dc = team_c2v<A, G>(g, s.C, s.L, m, r, W, clip, e, j, out);
+    //    of its variables follow by exact deltas.  A team takes two checks per
+    //    iteration where its warp has them: their chains of loads, phi and
+    //    shuffles interleave
+    auto put_c2v = [&](int dc, int e, int j, M_ out) {
       if (r < dc) {
         const int delta = fix_msg(s, out) - fix_msg(s, s.P[e]);
         s.P[e] = out;
         if (delta != 0) atomicAdd(&s.Lt[j], delta);
+      }
+    };
+    for (int t0 = warp * tpw; t0 < ncu; t0 += 2 * nw * tpw) {
+      const int ta = t0 + team, tb = ta + nw * tpw;
+      const int ma = ta < ncu ? s.cul[ta] : -1;
+      int ea, ja, eb, jb;
+      M_ oa, ob;
+      if (__any_sync(kFull, tb < ncu)) {
+        const int mb = tb < ncu ? s.cul[tb] : -1;
+        const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
+        const int dcb = team_c2v<A, G>(g, s.C, s.L, mb, r, W, clip, eb, jb, ob);
+        put_c2v(dca, ea, ja, oa);
+        put_c2v(dcb, eb, jb, ob);
+      } else {
+        const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
+        put_c2v(dca, ea, ja, oa);
       }
     }
     x.sync();
@@ -718,25 +731,42 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     //    written over the pair
     for (int w = tid; w < Mw; w += nt) s.cbits[w] = 0u;
     if (SCHED == kMELMD) {
-      for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
-        const int t = t0 + team;
-        int j = -1, k = 0;
+      // VN of lane r in pair t (-1: none) and the pair's owner k
+      auto pair_vn = [&](int t, int& k) -> int {
+        int j = -1;
+        k = 0;
         if (t < ncn) {
           const int2 ck = s.cnl[t];
           k = ck.y;
           const typename G::C cc = g.cn(ck.x);
           if (r < cc.d) j = g.cvn(cc, r);
         }
-        const D_ d = refresh_vn(j, true);
-        unsigned long long key = 0ull;
-        if (j >= 0 && j != s.sel[so + k]) key = ((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j);
+        return j;
+      };
+      auto pair_key = [&](int j, int k, D_ d) -> unsigned long long {
+        return (j >= 0 && j != s.sel[so + k]) ? (((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j))
+                                              : 0ull;
+      };
+      // two pairs per team and iteration where the warp has them (as above)
+      for (int t0 = warp * tpw; t0 < ncn; t0 += 2 * nw * tpw) {
+        const int ta = t0 + team, tb = ta + nw * tpw;
+        const bool two = __any_sync(kFull, tb < ncn);
+        int ka, kb = 0;
+        const int ja = pair_vn(ta, ka);
+        const int jb = two ? pair_vn(tb, kb) : -1;
+        const D_ da = refresh_vn(ja, true);
+        const D_ db = two ? refresh_vn(jb, true) : (D_)0;
+        unsigned long long keya = pair_key(ja, ka, da), keyb = pair_key(jb, kb, db);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           if (o >= W) continue;
-          const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
-          key = ok > key ? ok : key;
+          const unsigned long long oa = __shfl_xor_sync(kFull, keya, o);
+          const unsigned long long ob = __shfl_xor_sync(kFull, keyb, o);
+          keya = oa > keya ? oa : keya;
+          keyb = ob > keyb ? ob : keyb;
         }
-        if (r == 0 && t < ncn) s.cand[t] = key;
+        if (r == 0 && ta < ncn) s.cand[ta] = keya;
+        if (r == 0 && tb < ncn) s.cand[tb] = keyb;
       }
     } else {
       for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
