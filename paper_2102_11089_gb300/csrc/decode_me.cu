@@ -435,8 +435,12 @@ __device__ __forceinline__ MEState<A, CtaX> cta_state(const GraphDesc& gd, const
   return s;
 }
 
-// Decode one frame of code `gd` with thread group `x` on state `s`.
-template <int A, int SCHED, class G, class X>
+// Decode one frame of code `gd` with thread group `x` on state `s`.  kPair: a
+// check team takes two checks (and two LMD pairs) per loop iteration where its
+// warp has them, so that their dependency chains interleave; taken for frames
+// in shared memory only (with global-memory state the pairing measured 6-22 %
+// slower on 26k-bit codes).
+template <int A, int SCHED, class G, class X, bool kPair = false>
 __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const GraphDesc& gd, const G& g,
                                          const FrameIO& io, MEState<A, X>& s) {
   using M_ = typename Arith<A>::msg;
@@ -698,9 +702,8 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     // have passed the commit barrier now
     for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     // -- precomputed C2V of every affected check (once per check); the L~ sums
-    //    of its variables follow by exact deltas.  A team takes two checks per
-    //    iteration where its warp has them: their chains of loads, phi and
-    //    shuffles interleave
+    //    of its variables follow by exact deltas (two checks per team and
+    //    iteration with kPair)
     auto put_c2v = [&](int dc, int e, int j, M_ out) {
       if (r < dc) {
         const int delta = fix_msg(s, out) - fix_msg(s, s.P[e]);
@@ -708,20 +711,30 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         if (delta != 0) atomicAdd(&s.Lt[j], delta);
       }
     };
-    for (int t0 = warp * tpw; t0 < ncu; t0 += 2 * nw * tpw) {
-      const int ta = t0 + team, tb = ta + nw * tpw;
-      const int ma = ta < ncu ? s.cul[ta] : -1;
-      int ea, ja, eb, jb;
-      M_ oa, ob;
-      if (__any_sync(kFull, tb < ncu)) {
-        const int mb = tb < ncu ? s.cul[tb] : -1;
-        const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
-        const int dcb = team_c2v<A, G>(g, s.C, s.L, mb, r, W, clip, eb, jb, ob);
-        put_c2v(dca, ea, ja, oa);
-        put_c2v(dcb, eb, jb, ob);
-      } else {
-        const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
-        put_c2v(dca, ea, ja, oa);
+    if constexpr (kPair) {
+      for (int t0 = warp * tpw; t0 < ncu; t0 += 2 * nw * tpw) {
+        const int ta = t0 + team, tb = ta + nw * tpw;
+        const int ma = ta < ncu ? s.cul[ta] : -1;
+        int ea, ja, eb, jb;
+        M_ oa, ob;
+        if (__any_sync(kFull, tb < ncu)) {
+          const int mb = tb < ncu ? s.cul[tb] : -1;
+          const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
+          const int dcb = team_c2v<A, G>(g, s.C, s.L, mb, r, W, clip, eb, jb, ob);
+          put_c2v(dca, ea, ja, oa);
+          put_c2v(dcb, eb, jb, ob);
+        } else {
+          const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
+          put_c2v(dca, ea, ja, oa);
+        }
+      }
+    } else {
+      for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
+        const int t = t0 + team;
+        int e, j;
+        M_ out;
+        const int dc = team_c2v<A, G>(g, s.C, s.L, t < ncu ? s.cul[t] : -1, r, W, clip, e, j, out);
+        put_c2v(dc, e, j, out);
       }
     }
     x.sync();
@@ -747,26 +760,45 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         return (j >= 0 && j != s.sel[so + k]) ? (((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j))
                                               : 0ull;
       };
-      // two pairs per team and iteration where the warp has them (as above)
-      for (int t0 = warp * tpw; t0 < ncn; t0 += 2 * nw * tpw) {
-        const int ta = t0 + team, tb = ta + nw * tpw;
-        const bool two = __any_sync(kFull, tb < ncn);
-        int ka, kb = 0;
-        const int ja = pair_vn(ta, ka);
-        const int jb = two ? pair_vn(tb, kb) : -1;
-        const D_ da = refresh_vn(ja, true);
-        const D_ db = two ? refresh_vn(jb, true) : (D_)0;
-        unsigned long long keya = pair_key(ja, ka, da), keyb = pair_key(jb, kb, db);
+      // the team maximum of the pairs' keys
+      auto team_max = [&](unsigned long long key) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           if (o >= W) continue;
-          const unsigned long long oa = __shfl_xor_sync(kFull, keya, o);
-          const unsigned long long ob = __shfl_xor_sync(kFull, keyb, o);
-          keya = oa > keya ? oa : keya;
-          keyb = ob > keyb ? ob : keyb;
+          const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
+          key = ok > key ? ok : key;
         }
-        if (r == 0 && ta < ncn) s.cand[ta] = keya;
-        if (r == 0 && tb < ncn) s.cand[tb] = keyb;
+        return key;
+      };
+      if constexpr (kPair) {  // two pairs per team and iteration (as above)
+        for (int t0 = warp * tpw; t0 < ncn; t0 += 2 * nw * tpw) {
+          const int ta = t0 + team, tb = ta + nw * tpw;
+          const bool two = __any_sync(kFull, tb < ncn);
+          int ka, kb = 0;
+          const int ja = pair_vn(ta, ka);
+          const int jb = two ? pair_vn(tb, kb) : -1;
+          const D_ da = refresh_vn(ja, true);
+          const D_ db = two ? refresh_vn(jb, true) : (D_)0;
+          unsigned long long keya = pair_key(ja, ka, da), keyb = pair_key(jb, kb, db);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {  // both maxima at once (interleaved shuffles)
+            if (o >= W) continue;
+            const unsigned long long oa = __shfl_xor_sync(kFull, keya, o);
+            const unsigned long long ob = __shfl_xor_sync(kFull, keyb, o);
+            keya = oa > keya ? oa : keya;
+            keyb = ob > keyb ? ob : keyb;
+          }
+          if (r == 0 && ta < ncn) s.cand[ta] = keya;
+          if (r == 0 && two && tb < ncn) s.cand[tb] = keyb;
+        }
+      } else {
+        for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
+          const int t = t0 + team;
+          int k;
+          const int j = pair_vn(t, k);
+          const unsigned long long key = team_max(pair_key(j, k, refresh_vn(j, true)));
+          if (r == 0 && t < ncn) s.cand[t] = key;
+        }
       }
     } else {
       for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
@@ -879,7 +911,7 @@ __global__ void __launch_bounds__(TPB, MEBounds<A, TPB>::kMinBlocks) me_decode_k
   unsigned char* big = smem_raw + a.graph_smem;
   const CtaX x;
   MEState<A, CtaX> s = cta_state<A>(a.g, a, big, big + a.smem_per_frame, tab_int);
-  me_frame<A, SCHED, G, CtaX>(x, a, a.g, g, batch_io(a, blockIdx.x, A == kINT6 ? 1 : 4), s);
+  me_frame<A, SCHED, G, CtaX, true>(x, a, a.g, g, batch_io(a, blockIdx.x, A == kINT6 ? 1 : 4), s);
 }
 
 // Global-memory form: CTA c owns state slot c of a.gstate and decodes frames
