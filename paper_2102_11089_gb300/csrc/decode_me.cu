@@ -160,7 +160,8 @@ __host__ __device__ inline MESmall me_small(int M, int N, int n_p, int dvm, int 
 // shared scalars (misc area)
 struct MEMisc {
   int unsat;
-  int ncnu;  // affected (check, owner) pairs this step | distinct affected checks << 16
+  int ncnu;   // affected (check, owner) pairs this step | distinct affected checks << 16: checks of degree <= 8
+  int ncnu2;  // the same for checks of larger degree (kept from the back of the lists)
   int nsel[2];  // selected VNs of the two selection buffers (this step's, the next step's)
   int ncand;  // fill candidates gathered (reset at every step start)
   uint32_t thr, lo, hi;
@@ -461,6 +462,15 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
   const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
   const int Wv = team_width(gd.dv_max), tpv = 32 / Wv, vteam = lane / Wv, q = lane % Wv;
   const int Mw = (M + 31) / 32, Nw = (N + 31) / 32;
+  // Affected checks and (check, owner) pairs are kept in two degree classes:
+  // degree <= Ws from the front of their lists, handled by teams of Ws lanes,
+  // larger degrees from the back (capL - 1 downwards), by teams of W lanes.
+  // Codes whose checks all have degree <= 8 have one class, and so does the
+  // shared-memory form (kPair), whose registers the second class would spill.
+  constexpr bool kSplit = !kPair;
+  const int Ws = kSplit && W > 8 ? 8 : W;
+  const bool split = kSplit && W > Ws;
+  const int capL = np * (gd.dv_max > 1 ? gd.dv_max - 1 : 1);  // pairs of one step, at most
 
   int bad = 0;
   for (int n = tid; n < N; n += nt) {
@@ -490,6 +500,7 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
   if (tid == 0) {
     ms->unsat = 0;
     ms->ncnu = 0;
+    ms->ncnu2 = 0;
     ms->nsel[0] = 0;
     ms->nsel[1] = 0;
     ms->ncand = 0;
@@ -680,63 +691,77 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         const uint32_t bit = 1u << (m & 31);
         first = !(atomicOr(&s.cbits[m >> 5], bit) & bit);
       }
-      // list slots of the warp's pairs and new checks from one atomic on the
-      // packed counts (pairs in the low half, checks in the high half)
-      const unsigned bal = __ballot_sync(kFull, aff), bf = __ballot_sync(kFull, first);
-      int bases = 0;
-      if (lane == 0 && (bal | bf) != 0u) bases = atomicAdd(&ms->ncnu, __popc(bal) | (__popc(bf) << 16));
+      // list slots of the warp's pairs and new checks from one atomic per
+      // degree class on its packed counts (pairs in the low half, checks in
+      // the high half)
+      const bool big = split && aff && g.cn(m).d > Ws;
+      const unsigned bs = __ballot_sync(kFull, aff && !big), bb = kSplit ? __ballot_sync(kFull, big) : 0u;
+      const unsigned fs = __ballot_sync(kFull, first && !big), fb = kSplit ? __ballot_sync(kFull, first && big) : 0u;
+      int bases = 0, bases2 = 0;
+      if (lane == 0 && (bs | fs) != 0u) bases = atomicAdd(&ms->ncnu, __popc(bs) | (__popc(fs) << 16));
+      if (kSplit && lane == 0 && (bb | fb) != 0u) bases2 = atomicAdd(&ms->ncnu2, __popc(bb) | (__popc(fb) << 16));
       bases = __shfl_sync(kFull, bases, 0);
-      const int base = bases & 0xffff;
-      if (aff) s.cnl[base + __popc(bal & lanemask_lt())] = make_int2(m, k);
-      if (first) s.cul[(bases >> 16) + __popc(bf & lanemask_lt())] = m;
-      if (act && q == 0) {  // p's pairs are one block of the list: (first << 32) | count
+      if (kSplit) bases2 = __shfl_sync(kFull, bases2, 0);
+      const unsigned lt = lanemask_lt();
+      if (aff)
+        s.cnl[big ? capL - 1 - ((bases2 & 0xffff) + __popc(bb & lt)) : (bases & 0xffff) + __popc(bs & lt)] =
+            make_int2(m, k);
+      if (first) s.cul[big ? capL - 1 - ((bases2 >> 16) + __popc(fb & lt)) : (bases >> 16) + __popc(fs & lt)] = m;
+      if (act && q == 0) {  // p's pairs are one block of each list: (first, count) of both, 16 bits each
         const unsigned tm = (Wv == 32 ? kFull : ((1u << Wv) - 1u)) << (vteam * Wv);
         const unsigned below = (1u << (vteam * Wv)) - 1u;
-        s.best[k] = ((unsigned long long)(unsigned)(base + __popc(bal & below)) << 32) | (unsigned)__popc(bal & tm);
+        const unsigned long long f0 = (unsigned)((bases & 0xffff) + __popc(bs & below)), n0 = __popc(bs & tm);
+        const unsigned long long f1 = (unsigned)((bases2 & 0xffff) + __popc(bb & below)), n1 = __popc(bb & tm);
+        s.best[k] = f0 | (n0 << 16) | (f1 << 32) | (n1 << 48);
       }
     }
     x.sync();
     const int ncn = ms->ncnu & 0xffff, ncu = ms->ncnu >> 16;
+    const int ncn2 = ms->ncnu2 & 0xffff, ncu2 = ms->ncnu2 >> 16;
     // per-group counts of P': every warp summed them after the previous P'
     // barrier, and a warp that skipped the top-up met no barrier since; all
     // have passed the commit barrier now
     for (int i = tid; i < ng; i += nt) s.cntS[i] = 0;
     // -- precomputed C2V of every affected check (once per check); the L~ sums
-    //    of its variables follow by exact deltas (two checks per team and
-    //    iteration with kPair)
-    auto put_c2v = [&](int dc, int e, int j, M_ out) {
-      if (r < dc) {
-        const int delta = fix_msg(s, out) - fix_msg(s, s.P[e]);
-        s.P[e] = out;
-        if (delta != 0) atomicAdd(&s.Lt[j], delta);
-      }
-    };
-    if constexpr (kPair) {
-      for (int t0 = warp * tpw; t0 < ncu; t0 += 2 * nw * tpw) {
-        const int ta = t0 + team, tb = ta + nw * tpw;
-        const int ma = ta < ncu ? s.cul[ta] : -1;
-        int ea, ja, eb, jb;
-        M_ oa, ob;
-        if (__any_sync(kFull, tb < ncu)) {
-          const int mb = tb < ncu ? s.cul[tb] : -1;
-          const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
-          const int dcb = team_c2v<A, G>(g, s.C, s.L, mb, r, W, clip, eb, jb, ob);
-          put_c2v(dca, ea, ja, oa);
-          put_c2v(dcb, eb, jb, ob);
-        } else {
-          const int dca = team_c2v<A, G>(g, s.C, s.L, ma, r, W, clip, ea, ja, oa);
-          put_c2v(dca, ea, ja, oa);
+    //    of its variables follow by exact deltas.  One list of a degree class:
+    //    cnt checks, teams of Wc lanes (two checks per team and iteration
+    //    with kPair)
+    auto check_list = [&](int Wc, int cnt, bool back) {
+      const int tpc = 32 / Wc, tc = lane / Wc, rc = lane % Wc;
+      auto chk = [&](int t) { return t < cnt ? s.cul[back ? capL - 1 - t : t] : -1; };
+      auto put = [&](int dc, int e, int j, M_ out) {
+        if (rc < dc) {
+          const int delta = fix_msg(s, out) - fix_msg(s, s.P[e]);
+          s.P[e] = out;
+          if (delta != 0) atomicAdd(&s.Lt[j], delta);
+        }
+      };
+      if constexpr (kPair) {
+        for (int t0 = warp * tpc; t0 < cnt; t0 += 2 * nw * tpc) {
+          const int ta = t0 + tc, tb = ta + nw * tpc;
+          int ea, ja, eb, jb;
+          M_ oa, ob;
+          if (__any_sync(kFull, tb < cnt)) {
+            const int dca = team_c2v<A, G>(g, s.C, s.L, chk(ta), rc, Wc, clip, ea, ja, oa);
+            const int dcb = team_c2v<A, G>(g, s.C, s.L, chk(tb), rc, Wc, clip, eb, jb, ob);
+            put(dca, ea, ja, oa);
+            put(dcb, eb, jb, ob);
+          } else {
+            const int dca = team_c2v<A, G>(g, s.C, s.L, chk(ta), rc, Wc, clip, ea, ja, oa);
+            put(dca, ea, ja, oa);
+          }
+        }
+      } else {
+        for (int t0 = warp * tpc; t0 < cnt; t0 += nw * tpc) {
+          int e, j;
+          M_ out;
+          const int dc = team_c2v<A, G>(g, s.C, s.L, chk(t0 + tc), rc, Wc, clip, e, j, out);
+          put(dc, e, j, out);
         }
       }
-    } else {
-      for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
-        const int t = t0 + team;
-        int e, j;
-        M_ out;
-        const int dc = team_c2v<A, G>(g, s.C, s.L, t < ncu ? s.cul[t] : -1, r, W, clip, e, j, out);
-        put_c2v(dc, e, j, out);
-      }
-    }
+    };
+    check_list(Ws, ncu, false);
+    if (kSplit && ncu2 > 0) check_list(W, ncu2, true);
     x.sync();
     // -- L~_j, D_j next to the affected checks and of every p.  ME-LMD-CIRBP runs
     //    this over the (check i, owner p) pairs and also forms Alg. 6 lines 6-10's
@@ -744,72 +769,80 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     //    written over the pair
     for (int w = tid; w < Mw; w += nt) s.cbits[w] = 0u;
     if (SCHED == kMELMD) {
-      // VN of lane r in pair t (-1: none) and the pair's owner k
-      auto pair_vn = [&](int t, int& k) -> int {
-        int j = -1;
-        k = 0;
-        if (t < ncn) {
-          const int2 ck = s.cnl[t];
-          k = ck.y;
-          const typename G::C cc = g.cn(ck.x);
-          if (r < cc.d) j = g.cvn(cc, r);
-        }
-        return j;
-      };
       auto pair_key = [&](int j, int k, D_ d) -> unsigned long long {
         return (j >= 0 && j != s.sel[so + k]) ? (((unsigned long long)mkey(d) << 32) | (0xffffffffu - (uint32_t)j))
                                               : 0ull;
       };
-      // the team maximum of the pairs' keys
-      auto team_max = [&](unsigned long long key) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          if (o >= W) continue;
-          const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
-          key = ok > key ? ok : key;
-        }
-        return key;
-      };
-      if constexpr (kPair) {  // two pairs per team and iteration (as above)
-        for (int t0 = warp * tpw; t0 < ncn; t0 += 2 * nw * tpw) {
-          const int ta = t0 + team, tb = ta + nw * tpw;
-          const bool two = __any_sync(kFull, tb < ncn);
-          int ka, kb = 0;
-          const int ja = pair_vn(ta, ka);
-          const int jb = two ? pair_vn(tb, kb) : -1;
-          const D_ da = refresh_vn(ja, true);
-          const D_ db = two ? refresh_vn(jb, true) : (D_)0;
-          unsigned long long keya = pair_key(ja, ka, da), keyb = pair_key(jb, kb, db);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {  // both maxima at once (interleaved shuffles)
-            if (o >= W) continue;
-            const unsigned long long oa = __shfl_xor_sync(kFull, keya, o);
-            const unsigned long long ob = __shfl_xor_sync(kFull, keyb, o);
-            keya = oa > keya ? oa : keya;
-            keyb = ob > keyb ? ob : keyb;
+      // one pair list of a degree class: cnt pairs, teams of Wc lanes
+      auto pair_list = [&](int Wc, int cnt, bool back) {
+        const int tpc = 32 / Wc, tc = lane / Wc, rc = lane % Wc;
+        auto slot = [&](int t) { return back ? capL - 1 - t : t; };
+        // VN of lane rc in pair t (-1: none) and the pair's owner k
+        auto pair_vn = [&](int t, int& k) -> int {
+          int j = -1;
+          k = 0;
+          if (t < cnt) {
+            const int2 ck = s.cnl[slot(t)];
+            k = ck.y;
+            const typename G::C cc = g.cn(ck.x);
+            if (rc < cc.d) j = g.cvn(cc, rc);
           }
-          if (r == 0 && ta < ncn) s.cand[ta] = keya;
-          if (r == 0 && two && tb < ncn) s.cand[tb] = keyb;
+          return j;
+        };
+        if constexpr (kPair) {  // two pairs per team and iteration (as above)
+          for (int t0 = warp * tpc; t0 < cnt; t0 += 2 * nw * tpc) {
+            const int ta = t0 + tc, tb = ta + nw * tpc;
+            const bool two = __any_sync(kFull, tb < cnt);
+            int ka, kb = 0;
+            const int ja = pair_vn(ta, ka);
+            const int jb = two ? pair_vn(tb, kb) : -1;
+            const D_ da = refresh_vn(ja, true);
+            const D_ db = two ? refresh_vn(jb, true) : (D_)0;
+            unsigned long long keya = pair_key(ja, ka, da), keyb = pair_key(jb, kb, db);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {  // both team maxima at once (interleaved shuffles)
+              if (o >= Wc) continue;
+              const unsigned long long oa = __shfl_xor_sync(kFull, keya, o);
+              const unsigned long long ob = __shfl_xor_sync(kFull, keyb, o);
+              keya = oa > keya ? oa : keya;
+              keyb = ob > keyb ? ob : keyb;
+            }
+            if (rc == 0 && ta < cnt) s.cand[slot(ta)] = keya;
+            if (rc == 0 && two && tb < cnt) s.cand[slot(tb)] = keyb;
+          }
+        } else {
+          for (int t0 = warp * tpc; t0 < cnt; t0 += nw * tpc) {
+            const int t = t0 + tc;
+            int k;
+            const int j = pair_vn(t, k);
+            unsigned long long key = pair_key(j, k, refresh_vn(j, true));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {  // team maximum
+              if (o >= Wc) continue;
+              const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
+              key = ok > key ? ok : key;
+            }
+            if (rc == 0 && t < cnt) s.cand[slot(t)] = key;
+          }
         }
-      } else {
-        for (int t0 = warp * tpw; t0 < ncn; t0 += nw * tpw) {
-          const int t = t0 + team;
-          int k;
-          const int j = pair_vn(t, k);
-          const unsigned long long key = team_max(pair_key(j, k, refresh_vn(j, true)));
-          if (r == 0 && t < ncn) s.cand[t] = key;
-        }
-      }
+      };
+      pair_list(Ws, ncn, false);
+      if (kSplit && ncn2 > 0) pair_list(W, ncn2, true);
     } else {
-      for (int t0 = warp * tpw; t0 < ncu; t0 += nw * tpw) {
-        const int t = t0 + team;
-        int j = -1;
-        if (t < ncu) {
-          const typename G::C cc = g.cn(s.cul[t]);
-          if (r < cc.d) j = g.cvn(cc, r);
+      auto vn_list = [&](int Wc, int cnt, bool back) {
+        const int tpc = 32 / Wc, tc = lane / Wc, rc = lane % Wc;
+        for (int t0 = warp * tpc; t0 < cnt; t0 += nw * tpc) {
+          const int t = t0 + tc;
+          int j = -1;
+          if (t < cnt) {
+            const typename G::C cc = g.cn(s.cul[back ? capL - 1 - t : t]);
+            if (rc < cc.d) j = g.cvn(cc, rc);
+          }
+          refresh_vn(j, false);
         }
-        refresh_vn(j, false);
-      }
+      };
+      vn_list(Ws, ncu, false);
+      if (kSplit && ncu2 > 0) vn_list(W, ncu2, true);
     }
     // the selected VNs go to the last warps, which have the fewest pair teams
     for (int k0 = (nw - 1 - warp) * 32; k0 < nsel; k0 += nt) {
@@ -819,7 +852,10 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
     x.sync();
     // the pair and check counts were read after the commit barrier; the next
     // commit phase, which counts again, starts after at least one more barrier
-    if (tid == 0) ms->ncnu = 0;
+    if (tid == 0) {
+      ms->ncnu = 0;
+      ms->ncnu2 = 0;
+    }
     count += done;
     ++step;
     if (check_due(left, a.check_interval, done) && ms->unsat == 0) break;
@@ -835,11 +871,16 @@ __device__ __forceinline__ void me_frame(const X& x, const DecodeArgs& a, const 
         int j = 0;
         if (k < nsel) {
           const int p = s.sel[so + k];
-          const unsigned long long rg = s.best[k];
-          const int first = (int)(rg >> 32), npair = (int)(rg & 0xffffffffull);
+          const unsigned long long rg = s.best[k];  // p's pairs in both degree classes
+          const int f0 = (int)(rg & 0xffff), n0 = (int)((rg >> 16) & 0xffff);
+          const int f1 = (int)((rg >> 32) & 0xffff), n1 = (int)(rg >> 48);
           unsigned long long bk = 0ull;
-          for (int i = first; i < first + npair; ++i) {
+          for (int i = f0; i < f0 + n0; ++i) {
             const unsigned long long v = s.cand[i];
+            bk = v > bk ? v : bk;
+          }
+          for (int i = f1; kSplit && i < f1 + n1; ++i) {
+            const unsigned long long v = s.cand[capL - 1 - i];
             bk = v > bk ? v : bk;
           }
           if (g.vn(p).d == 1) {
