@@ -81,6 +81,22 @@ def test_large_bg2_z128_int6_bitexact(schedule, n_p):
     assert_bitexact(g, o, schedule)
 
 
+@pytest.mark.parametrize("form", ["global", "cluster"])
+@pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "me-cirbp"])
+def test_two_degree_classes_at_largest_n_p_int6_bitexact(schedule, form):
+    # BG2-shaped Z = 64 (checks of degree 4 to 10, VNs up to degree 23): the
+    # affected checks and pairs of a step fill both degree-class lists, and at
+    # N_P = 384 the lists come close to their shared capacity N_P (d_v,max - 1)
+    spec = qc("bg2", 64)
+    code = make_code(spec)
+    q = wl.quantize_llrs(llrs(spec, 3, 1.25, 41), 0.5)
+    kw = dict(schedule=schedule, max_updates=2 * code.E, gamma=0.1, n_p=384, n_g=16, seed=12,
+              form=L.FORM_GLOBAL if form == "global" else L.FORM_CLUSTER)
+    g = run_gpu(code, q, torch, arith="int6", **kw)
+    o = run_oracle(spec, q, "int6", **{k: v for k, v in kw.items() if k != "form"})
+    assert_bitexact(g, o, schedule)
+
+
 @pytest.mark.parametrize("schedule", ["me-lmd-cirbp", "lmd-cirbp"])
 def test_large_bg1_z384_n26112(schedule):
     # the 26,112-bit BG1-shaped code: frame state ~1.3 MB (FP32), global-memory form
