@@ -47,7 +47,15 @@ struct SEState {
   uint32_t* Rblk;    // largest per-check residual key per block of 32 checks (RBP, CIRBP)
   uint32_t* Rdirty;
   int16_t* tab;
+  int32_t* Lt;       // CIRBP, LMD-CIRBP: sum over the edges of each VN of L~^C, exact integer
+  float fx, ifx;     // FP32 fixed point of those sums: 2^k and 2^-k
 };
+
+// message -> exact integer term of the L~ sum, and L~ = lambda + that sum
+__device__ __forceinline__ int se_fix(const SEState<kFP32>& s, float x) { return __float2int_rn(x * s.fx); }
+__device__ __forceinline__ int se_fix(const SEState<kINT6>&, int8_t x) { return (int)x; }
+__device__ __forceinline__ float se_lt(const SEState<kFP32>& s, int n) { return s.lam[n] + (float)s.Lt[n] * s.ifx; }
+__device__ __forceinline__ int16_t se_lt(const SEState<kINT6>& s, int n) { return (int16_t)(s.lam[n] + s.Lt[n]); }
 
 // Upper level of the global argmaxes: blk[b] is the largest key of block b (32
 // entries).  A key that grows raises its block's entry at once; a key that
@@ -218,11 +226,16 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   using L_ = typename Arith<A>::llr;
   using D_ = typename Arith<A>::dval;
   constexpr bool kNeedR = SCHED != kLMD;
+  // L~_j of the refreshed VNs from sums kept up to date by the check updates
+  // (integers: the sum does not depend on the order of the updates; FP32
+  // messages in fixed point x 2^k, d_v,max * llr_clip * 2^k < 2^30) instead
+  // of d_v(j) reads of L~^C per refreshed VN
+  constexpr bool kLt = SCHED == kLMD || SCHED == kCIRBP;
   constexpr bool kDblk = kVs && SCHED == kCIRBP;                   // global argmax of D every update
   constexpr bool kRblk = kVs && (SCHED == kCIRBP || SCHED == kRBP);  // global argmax of the residuals
   const int lane = threadIdx.x & 31;
   const int N = gd.N, E = gd.E, M = gd.M;
-  const SELayout ly = se_layout(A, M, N, E, kNeedR);
+  const SELayout ly = se_layout(A, M, N, E, SCHED);
   SEState<A> s;
   s.C = (M_*)(ebase + ly.C);
   s.P = (M_*)(ebase + ly.P);
@@ -237,6 +250,12 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
   s.Rblk = (uint32_t*)(vbase + ly.Rblk);
   s.Rdirty = (uint32_t*)(vbase + ly.Rdirty);
   s.tab = (int16_t*)(vbase + ly.tab);
+  s.Lt = (int32_t*)(vbase + ly.Lt);
+  {
+    const int k = min(24, 29 - ilogbf((float)gd.dv_max * a.llr_clip));
+    s.fx = __int_as_float((127 + k) << 23);
+    s.ifx = __int_as_float((127 - k) << 23);
+  }
   const float clip = a.llr_clip;
   const int W = team_width(gd.dc_max), tpw = 32 / W, team = lane / W, r = lane % W;
 
@@ -284,7 +303,21 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     if (r < dc) s.P[e] = out;
   }
   __syncwarp();
-  for (int n = lane; n < N; n += 32) s.D[n] = ci_val(s, s.L[n], vn_total<A, G>(g, s.lam, s.P, n));
+  for (int n = lane; n < N; n += 32) {
+    if (kLt) {
+      const typename G::V v = g.vn(n);
+      int acc = 0;
+      for (int k = 0; k < v.d; ++k) {
+        int e, m;
+        g.vedge(v, k, e, m);
+        acc += se_fix(s, s.P[e]);
+      }
+      s.Lt[n] = acc;
+      s.D[n] = ci_val(s, s.L[n], se_lt(s, n));
+    } else {
+      s.D[n] = ci_val(s, s.L[n], vn_total<A, G>(g, s.lam, s.P, n));
+    }
+  }
   uint32_t unsat = 0;
   for (int m0 = 0; m0 < M; m0 += 32) {
     const int m = m0 + lane;
@@ -405,6 +438,14 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
     //    new V2C inputs and precomputed C2V (eq. 2), then L~_j and D_j of its
     //    variables j != n* (also the LMD candidates)
     const int nref = dv - 1;
+    // new L~^C of edge e (towards j); with kLt its L~ sum follows by the exact delta
+    auto put_p = [&](int e, int j, M_ out) {
+      if (kLt) {
+        const int delta = se_fix(s, out) - se_fix(s, s.P[e]);
+        if (delta != 0) atomicAdd(&s.Lt[j], delta);
+      }
+      s.P[e] = out;
+    };
     uint32_t ck = 0, cidx = 0xffffffffu;
     uint32_t rck = 0, rcidx = 0xffffffffu;
     if (nref <= tpw) {  // one pass of teams
@@ -415,12 +456,12 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
       const int dc = team_c2v<A, G>(g, s.C, s.L, team < nref ? m : -1, r, W, clip, e, j, out);
       const bool mine = r < dc && j != nstar;
       if (mine) {
-        s.P[e] = out;
+        put_p(e, j, out);
         if (kLMDR) am_update(rck, rcidx, rkey(out, s.C[e]), (uint32_t)e);  // Alg. 2 line 9
       }
       __syncwarp();
       if (mine) {
-        const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
+        const D_ d = ci_val(s, s.L[j], kLt ? se_lt(s, j) : vn_total<A, G>(g, s.lam, s.P, j));
         set_D(j, d);
         am_update(ck, cidx, mkey(d), (uint32_t)j);
       }
@@ -433,7 +474,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
         M_ out;
         const int dc = team_c2v<A, G>(g, s.C, s.L, i < nref ? m : -1, r, W, clip, e, j, out);
         if (r < dc && j != nstar) {
-          s.P[e] = out;
+          put_p(e, j, out);
           if (kLMDR) am_update(rck, rcidx, rkey(out, s.C[e]), (uint32_t)e);  // Alg. 2 line 9
         }
       }
@@ -447,7 +488,7 @@ __device__ __forceinline__ void se_frame(const DecodeArgs& a, const GraphDesc& g
         if (r >= cc.d) continue;
         const int j = g.cvn(cc, r);
         if (j == nstar) continue;
-        const D_ d = ci_val(s, s.L[j], vn_total<A, G>(g, s.lam, s.P, j));
+        const D_ d = ci_val(s, s.L[j], kLt ? se_lt(s, j) : vn_total<A, G>(g, s.lam, s.P, j));
         set_D(j, d);
         am_update(ck, cidx, mkey(d), (uint32_t)j);
       }
@@ -521,7 +562,7 @@ __global__ void __launch_bounds__(512) se_decode_kernel(const DecodeArgs a) {
   if (b >= a.batch) return;
   unsigned char* vbase = smem_raw + a.graph_smem + (size_t)warp * a.smem_per_frame;
   se_frame<A, SCHED, G, true>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), vbase,
-                              vbase + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal);
+                              vbase + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED).vtotal);
 }
 
 // Global-memory form (frame state larger than shared memory): every warp owns
@@ -537,7 +578,7 @@ __global__ void __launch_bounds__(256, 4) se_decode_kernel_gs(const DecodeArgs a
   const int64_t slot = (int64_t)blockIdx.x * a.frames_per_cta + warp;
   const int64_t slots = (int64_t)gridDim.x * a.frames_per_cta;
   unsigned char* base = (unsigned char*)a.gstate + slot * a.gstate_stride;
-  unsigned char* ebase = base + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED != kLMD).vtotal;
+  unsigned char* ebase = base + se_layout(A, a.g.M, a.g.N, a.g.E, SCHED).vtotal;
   for (int64_t b = slot; b < a.batch; b += slots)
     se_frame<A, SCHED, G, false>(a, a.g, g, batch_io(a, b, A == kINT6 ? 1 : 4), base, ebase);
 }
@@ -600,7 +641,7 @@ __global__ void __launch_bounds__(32) se_queue_kernel(const QueueArgs q) {
     io.trace = nullptr;
     io.max_updates = it.max_updates;
     io.frame = it.frame_index;
-    const SELayout ly = se_layout(A, s_gd.M, s_gd.N, s_gd.E, SCHED != kLMD);
+    const SELayout ly = se_layout(A, s_gd.M, s_gd.N, s_gd.E, SCHED);
     unsigned char* base = ly.total <= q.smem_state_bytes ? sstate : gslot;
     se_frame<A, SCHED, QCGraph, false>(q.a, s_gd, g, io, base, base + ly.vtotal);
   }
@@ -673,11 +714,11 @@ cudaError_t launch_se_queue(const QueueArgs& q, int arith, int grid, size_t smem
 }
 
 size_t se_smem_per_frame(int arith, int sched, const GraphDesc& g) {
-  return (size_t)se_layout(arith, g.M, g.N, g.E, sched != kLMD).total;
+  return (size_t)se_layout(arith, g.M, g.N, g.E, sched).total;
 }
 
 size_t se_vregion_bytes(int arith, int sched, const GraphDesc& g) {
-  return (size_t)se_layout(arith, g.M, g.N, g.E, sched != kLMD).vtotal;
+  return (size_t)se_layout(arith, g.M, g.N, g.E, sched).vtotal;
 }
 
 cudaError_t launch_se(const DecodeArgs& a, int arith, int sched, cudaStream_t s) {

@@ -162,12 +162,16 @@ inline __host__ __device__ int graph_smem_bytes(const GraphDesc& d) {
 // block of 32 VNs / 32 checks (the upper level of the global argmax of CIRBP
 // and RBP), with dirty bits of blocks whose maximum may have dropped.
 struct SELayout {
-  int lam, L, D, Rmax, Ridx, par, Dblk, Ddirty, Rblk, Rdirty, tab, vtotal;
+  int lam, L, D, Lt, Rmax, Ridx, par, Dblk, Ddirty, Rblk, Rdirty, tab, vtotal;
   int C, P, etotal;
   int total;
 };
 
-inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bool need_r) {
+// Per-frame state of the single-edge schedules: the residual maxima for the
+// schedules that search residuals, the exact L~ sums (Lt) for those that read D.
+inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, int sched) {
+  const bool need_r = sched != kLMD;
+  const bool need_lt = sched == kLMD || sched == kCIRBP;
   const int msg = arith == kINT6 ? 1 : 4;
   const int llr = arith == kINT6 ? 2 : 4;
   const int dv = arith == kINT6 ? 2 : 4;
@@ -176,6 +180,7 @@ inline __host__ __device__ SELayout se_layout(int arith, int M, int N, int E, bo
   l.lam = o; o = align16(o + N * llr);
   l.L = o; o = align16(o + N * llr);
   l.D = o; o = align16(o + N * dv);
+  l.Lt = o; o = align16(o + (need_lt ? N * 4 : 0));
   l.Rmax = o; o = align16(o + (need_r ? M * msg : 0));
   l.Ridx = o; o = align16(o + (need_r ? M * 4 : 0));
   l.par = o; o = align16(o + ((M + 31) / 32) * 4);
