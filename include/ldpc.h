@@ -241,7 +241,7 @@ ldpc_status_t ldpc_encode(const ldpc_code_t *code, const uint8_t *info, int64_t 
  * Execution form (params->form = LDPC_FORM_AUTO): frame state in shared
  * memory when it fits one CTA (single-edge frames: when shared memory holds
  * at least eight per SM, else global memory; the split form only on request);
- * else, for the multi-edge schedules and a batch
+ * else, for the multi-edge schedules in 6-bit mode or with n_p >= 128 and a batch
  * of at most twice the resident clusters (SMs / cluster size), spread over the
  * shared memory of a thread-block cluster (the smallest of 2, 4, 8 or 16 CTAs
  * that holds it and can be resident); else global memory.  A cluster size in
